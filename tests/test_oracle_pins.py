@@ -1,0 +1,214 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+- hand-derived worked examples (tests/golden/worked_examples.json);
+- exhaustive enumeration of every integer domain value (oracle/definition.py,
+  exact rationals) on many tiny instances, with random tabu/aspiration states;
+- a dense grid over continuous domains: no admissible point beats the reported
+  best (the step-function claim of Sec. 3.1);
+- binary variables scored as integers in [0, 1] give the flip result;
+- closed form of a single-row problem;
+- trajectory invariant: each applied move's score equals the penalty sum
+  recomputed from the whole residual vector before and after (scipy.sparse);
+- determinism across thread counts.
+"""
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from conftest import golden_cases, problem_from_case
+from oracle import definition
+from oracle.oracle import Oracle
+from paper_2605_05086_gb300 import instances as inst
+
+
+def _state(prob, case):
+    return (np.array(case["x"], float), np.array(case["w"], np.int32),
+            np.array(case["tabu_inc"], np.int64), np.array(case["tabu_dec"], np.int64),
+            int(case["iter"]), int(case["best_nviol"]))
+
+
+@pytest.mark.parametrize("case", golden_cases(), ids=lambda c: c["name"])
+def test_worked_examples(case):
+    prob = problem_from_case(case)
+    tol = case.get("feas_tol", 1e-9)
+    orc = Oracle(prob, feas_tol=tol)
+    x, w, ti, td, it, bn = _state(prob, case)
+    _, _, nviol = orc.residuals(x)
+    xh, sh, dc = orc.best_shift(x, w, ti, td, it, nviol, bn)
+    got = [[float(a), int(b), int(c)] for a, b, c in zip(xh, sh, dc)]
+    assert got == [[float(a), int(b), int(c)] for a, b, c in case["expect"]]
+    if "expect_best_var" in case:
+        assert int(np.argmax(sh)) == case["expect_best_var"]
+    # every listed domain score agrees with the exact definition
+    rows = definition.normalised_rows(prob, tol)
+    xf = [F(float(v)) for v in x]
+    for key in ("domain_scores_half", "candidate_scores_half", "domain_scores_half_var0"):
+        for v, s in case.get(key, {}).items():
+            assert definition.score(rows, xf, w, 0, F(v))[0] == s, (key, v)
+    if "candidates_var0" in case:
+        assert definition.candidate_values(prob, x, 0, tol) == {F(v) for v in case["candidates_var0"]}
+    if all(t != inst.VAR_CONT for t in case["vtype"]):
+        _check_against_exhaustive(prob, x, w, ti, td, it, nviol, bn, tol, xh, sh, dc)
+
+
+def _check_against_exhaustive(prob, x, w, ti, td, it, nviol, bn, tol, xh, sh, dc):
+    """The oracle's score is the maximum over the whole domain, its value attains it,
+    and it is the closest maximiser among the bounds and breakpoints."""
+    ex = definition.exhaustive_max(prob, x, w, ti, td, it, nviol, bn, feas_tol=tol)
+    for j, (best, arg) in enumerate(ex):
+        if best is None or best <= 0:
+            assert (float(xh[j]), int(sh[j]), int(dc[j])) == (float(x[j]), 0, 0), j
+            continue
+        assert int(sh[j]) == best, j
+        v = int(xh[j])
+        assert v == xh[j] and v in arg and int(dc[j]) == arg[v], j
+        cands = definition.candidate_values(prob, x, j, tol)
+        tied = [u for u in arg if F(u) in cands]
+        assert v == min(tied, key=lambda u: (abs(u - float(x[j])), u)), j
+
+
+def _random_tabu(rng, n, it):
+    ti = rng.integers(0, it + 3, size=n).astype(np.int64)
+    td = rng.integers(0, it + 3, size=n).astype(np.int64)
+    return ti, td
+
+
+@pytest.mark.parametrize("seed", range(60))
+@pytest.mark.parametrize("dyadic", [False, True])
+def test_exhaustive_integer_domains(seed, dyadic):
+    prob = inst.gen_tiny_mixed(seed, n=6, m=5, max_len=4, dom=12, cont_frac=0.0, dyadic=dyadic)
+    rng = np.random.default_rng(1000 + seed)
+    tol = 0.0 if dyadic else 1e-9
+    orc = Oracle(prob, feas_tol=tol)
+    x = prob.x0
+    w = rng.integers(1, 4, size=orc.mn).astype(np.int32)
+    it = 2
+    ti, td = _random_tabu(rng, prob.n, it)
+    _, _, nviol = orc.residuals(x)
+    bn = nviol - int(rng.integers(0, 2))
+    xh, sh, dc = orc.best_shift(x, w, ti, td, it, nviol, bn)
+    _check_against_exhaustive(prob, x, w, ti, td, it, nviol, bn, tol, xh, sh, dc)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_continuous_grid_never_beats_best(seed):
+    prob = inst.gen_tiny_mixed(seed, n=5, m=5, max_len=4, dom=6, cont_frac=0.5, dyadic=True)
+    rng = np.random.default_rng(2000 + seed)
+    orc = Oracle(prob, feas_tol=0.0)
+    x = prob.x0
+    w = rng.integers(1, 4, size=orc.mn).astype(np.int32)
+    it = 1
+    ti, td = _random_tabu(rng, prob.n, it)
+    _, _, nviol = orc.residuals(x)
+    bn = nviol
+    xh, sh, dc = orc.best_shift(x, w, ti, td, it, nviol, bn)
+    rows = definition.normalised_rows(prob, 0.0)
+    xf = [F(float(v)) for v in x]
+    for j in range(prob.n):
+        if prob.vtype[j] != inst.VAR_CONT:
+            continue
+        if sh[j] > 0:
+            s, d = definition.score(rows, xf, w, j, F(float(xh[j])))
+            assert (s, d) == (int(sh[j]), int(dc[j]))
+            assert definition.admissible(F(float(xh[j])), xf[j], j, d, ti, td, it, nviol, bn)
+        lo, hi = F(float(prob.lb[j])), F(float(prob.ub[j]))
+        grid = [lo + (hi - lo) * F(q, 256) for q in range(257)]
+        for g in grid:
+            if g == xf[j]:
+                continue
+            s, d = definition.score(rows, xf, w, j, g)
+            if definition.admissible(g, xf[j], j, d, ti, td, it, nviol, bn):
+                assert s <= max(int(sh[j]), 0), (j, g, s, sh[j])
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_binary_equals_integer_zero_one(seed):
+    prob = inst.gen_tiny_mixed(seed, n=8, m=6, max_len=5, dom=5, cont_frac=0.0, dyadic=False)
+    rng = np.random.default_rng(3000 + seed)
+    orc = Oracle(prob)
+    x = prob.x0
+    w = rng.integers(1, 4, size=orc.mn).astype(np.int32)
+    ti, td = _random_tabu(rng, prob.n, 1)
+    _, _, nviol = orc.residuals(x)
+    a = orc.best_shift(x, w, ti, td, 1, nviol, nviol)
+    prob2 = inst.from_triplets("as_int", prob.n, prob.m,
+                               np.repeat(np.arange(prob.m), np.diff(prob.row_ptr)), prob.col_idx,
+                               prob.row_val, prob.lb, prob.ub, prob.obj, prob.rhs,
+                               np.where(prob.vtype == inst.VAR_BIN, inst.VAR_INT, prob.vtype), prob.sense,
+                               x0=prob.x0)
+    b = Oracle(prob2).best_shift(x, w, ti, td, 1, nviol, nviol)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("a,b,xbar,ub", [(3, 10, 9, 12), (2, 7, 8, 8), (5, 4, 3, 6), (1, 0, 5, 5)])
+def test_single_row_closed_form(a, b, xbar, ub):
+    """One integer var, one row a*x <= b violated at xbar: the best shift is the
+    largest feasible value floor(b/a) (score +w, i.e. 2 half units) when it is in
+    the domain; values between it and xbar only reduce the violation (+w/2)."""
+    prob = inst.from_triplets("single", 1, 1, [0], [0], [float(a)], lb=[0], ub=[ub], obj=[1],
+                              rhs=[float(b)], vtype=[inst.VAR_INT], sense=[inst.ROW_LE], x0=[xbar])
+    orc = Oracle(prob)
+    x = np.array([float(xbar)])
+    _, _, nviol = orc.residuals(x)
+    assert nviol == 1
+    xh, sh, dc = orc.best_shift(x, np.ones(1, np.int32), np.zeros(1, np.int64), np.zeros(1, np.int64), 0, 1, 1)
+    assert xh[0] == b // a and sh[0] == 2 and dc[0] == -1
+
+
+def _normalised_matrix(prob):
+    """Independent normalisation with scipy: returns (A_norm csr, b_norm)."""
+    A = sp.csr_matrix((prob.row_val, prob.col_idx, prob.row_ptr), shape=(prob.m, prob.n))
+    blocks, rhs = [], []
+    for i in range(prob.m):
+        s = prob.sense[i]
+        if s in (inst.ROW_LE, inst.ROW_EQ):
+            blocks.append(A[i]); rhs.append(prob.rhs[i])
+        if s in (inst.ROW_GE, inst.ROW_EQ):
+            blocks.append(-A[i]); rhs.append(-prob.rhs[i])
+    return sp.vstack(blocks).tocsr(), np.array(rhs)
+
+
+@pytest.mark.parametrize("which", ["setcover", "tiny_int"])
+def test_move_score_equals_recomputed_penalty(which):
+    if which == "setcover":
+        prob = inst.gen_setcover(seed=3, n=300, m=150, k=8)
+        iters = 300
+    else:
+        prob = inst.gen_tiny_mixed(7, n=12, m=10, max_len=5, dom=10, dyadic=False)
+        iters = 200
+    orc = Oracle(prob)
+    An, bn = _normalised_matrix(prob)
+    st = orc.initial_state()
+    for _ in range(iters):
+        x0 = st["x"].copy()
+        w0 = st["w"].copy()
+        tr = orc.run(st, tenure=5, n_iters=1, stop_at_feasible=True)
+        if len(tr["var"]) == 0:
+            break
+        r0 = An @ x0 - bn
+        r1 = An @ st["x"] - bn
+        v0, v1 = r0 > 0, r1 > 0
+        p = np.where(~v0 & v1, -2 * w0, np.where(v0 & ~v1, 2 * w0,
+                     np.where(v0 & v1 & (r1 < r0), w0, np.where(v0 & v1 & (r1 > r0), -w0, 0))))
+        if tr["var"][0] >= 0:
+            assert int(p.sum()) == int(tr["s_half"][0]) > 0
+            assert np.count_nonzero(x0 != st["x"]) == 1
+        else:
+            assert np.array_equal(st["x"], x0)
+            assert np.array_equal(st["w"] - w0, v0.astype(np.int32))
+        assert int(v1.sum()) == int(tr["nviol_after"][0])
+        assert (st["w"] >= w0).all()
+
+
+def test_thread_count_does_not_change_trajectory():
+    prob = inst.gen_setcover(seed=1, n=500, m=250, k=8)
+    orc = Oracle(prob)
+    a, b = orc.initial_state(), orc.initial_state()
+    ta = orc.run(a, tenure=10, n_iters=200, nthreads=1)
+    tb = orc.run(b, tenure=10, n_iters=200, nthreads=4)
+    for k in ta:
+        assert np.array_equal(ta[k], tb[k])
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["w"], b["w"])
