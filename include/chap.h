@@ -1,0 +1,236 @@
+/*
+ * chap.h -- C ABI of the GB300 best-shift tabu search library (libchap.so).
+ *
+ * The library evaluates, for every variable of a MIP at the current assignment,
+ * its best shift move (Sec. 3.1 "Best Shift Moves", Eq. best_move, Algorithm 1
+ * of "CHAP: A Hybrid GPU-CPU Heuristic for MIP"), picks the best admissible move
+ * under tabu and aspiration rules, and applies it with an incremental update of
+ * the row residuals (Sec. 3.1 "Memory Considerations").  Every step runs in
+ * hand-written CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *  - Status codes only; no exception or abort crosses the ABI.  After an error
+ *    chap_last_error(handle) gives a message valid until the next call on that
+ *    handle.
+ *  - Streams: every device operation is ordered on the CUDA stream given to
+ *    chap_bs_create (NULL = the legacy default stream).  Calls that return host
+ *    data synchronise that stream before returning; calls with device outputs
+ *    do not.
+ *  - Memory: chap_bs_create copies everything it needs; the caller keeps
+ *    ownership of every buffer it passes.  Output buffers are caller-owned and
+ *    live in host or device memory as the `mem` argument says.
+ *  - Values cross the ABI as doubles; integer values are exact below 2^53.
+ *  - Normalised rows (Sec. 3.1, "Memory Considerations", second point): every
+ *    original row i is turned into "<=" rows, in this canonical order: a "<="
+ *    row gives (a_i, b_i); a ">=" row gives (-a_i, -b_i); an "=" row gives
+ *    (a_i, b_i) and then (-a_i, -b_i).  Constraint weights w and violation
+ *    counts are per normalised row; m_norm = m + (number of "=" rows).
+ *  - Violation of a normalised row: r = a.x - b > eps, where eps = 0 on an
+ *    integral row (integer coefficients below 2^31 in magnitude, integer rhs,
+ *    only binary/integer variables with finite bounds, and sum |a| max(|l|,|u|)
+ *    + |b| <= 2^52) and eps = feas_tol * max(1, |b|) on any other row.
+ *    Integral rows keep their residual in exact int64 arithmetic.
+ *  - Scores are int64 counts of half weights ("score_half" = 2 * s_j with s_j of
+ *    Sec. 3.1 "Scoring Functions"), so integer weights give exact scores.
+ */
+#ifndef CHAP_H
+#define CHAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CHAP_API __attribute__((visibility("default")))
+#else
+#define CHAP_API
+#endif
+
+typedef int32_t chap_status;
+enum {
+    CHAP_OK = 0,
+    CHAP_E_INVALID = 1,     /* bad argument or malformed problem */
+    CHAP_E_OOM = 2,         /* device or host allocation failed */
+    CHAP_E_CUDA = 3,        /* a CUDA runtime call failed */
+    CHAP_E_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+    CHAP_E_STATE = 5,       /* call not valid in the handle's current state */
+    CHAP_E_UNSUPPORTED = 6  /* valid input outside what this build handles */
+};
+
+enum { CHAP_VAR_BIN = 0, CHAP_VAR_INT = 1, CHAP_VAR_CONT = 2 };
+enum { CHAP_ROW_LE = 0, CHAP_ROW_GE = 1, CHAP_ROW_EQ = 2 };
+enum { CHAP_MEM_HOST = 0, CHAP_MEM_DEVICE = 1 };
+
+/*
+ * The MIP of Sec. 3.1: min c^T x s.t. each row (<=, >=, =) b, l <= x <= u,
+ * x_j integer for binary/integer j.  All arrays are HOST memory.
+ *  row_ptr[m+1], col_idx[nnz], row_val[nnz]: CSR of A, column indices strictly
+ *      increasing inside each row.
+ *  col_ptr[n+1], row_idx[nnz], col_val[nnz]: CSC of the same A, row indices
+ *      strictly increasing inside each column; must equal the CSR transposed.
+ *  lb[n], ub[n]: bounds (+-infinity allowed for integer/continuous variables;
+ *      a binary variable's bounds must lie in {0, 1}; integer bounds integral).
+ *  obj[n] (may be NULL: zeros), rhs[m] (finite), vtype[n] (CHAP_VAR_*),
+ *  sense[m] (CHAP_ROW_*).
+ */
+typedef struct chap_problem {
+    int32_t n, m;
+    int64_t nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const double *row_val;
+    const int64_t *col_ptr;
+    const int32_t *row_idx;
+    const double *col_val;
+    const double *lb, *ub, *obj, *rhs;
+    const uint8_t *vtype, *sense;
+} chap_problem;
+
+/*
+ * Options.  feas_tol: tolerance of non-integral rows (default 1e-9).
+ * tenure: after a move at iteration k that increases x_j, decreasing x_j is tabu
+ * while iter < k + 1 + tenure, and symmetrically (default 10).  max_iters: limit
+ * of chap_tabu_run (default 1000).  graph_iters: iterations recorded in one CUDA
+ * graph replay (default 64).  stop_at_feasible: chap_tabu_run stops at the first
+ * iteration that leaves no violated row (default 1).
+ */
+typedef struct chap_options {
+    double feas_tol;
+    int32_t tenure;
+    int32_t graph_iters;
+    int64_t max_iters;
+    int32_t stop_at_feasible;
+    int32_t reserved[7];
+} chap_options;
+
+/* One move.  var = -1 means "no admissible variable has a positive score": the
+ * iteration instead adds 1 to the weight of every violated normalised row. */
+typedef struct chap_move {
+    int32_t var;
+    int32_t dnviol;        /* change of the number of violated normalised rows */
+    int64_t score_half;    /* 2 * s_j of the move */
+    double old_value;
+    double new_value;
+} chap_move;
+
+typedef struct chap_tabu_result {
+    int64_t iters;            /* iterations run by this call */
+    int64_t moves;            /* of which applied moves (the rest updated weights) */
+    int64_t feasible_iter;    /* iteration count at which nviol first reached 0, else -1 */
+    int64_t final_nviol;
+    int64_t best_nviol;
+    double seconds;           /* wall time of the call */
+    double time_to_feasible_s;/* device time from the call's start to feasibility, else -1 */
+    double objective;         /* c^T x at return */
+} chap_tabu_result;
+
+/* Sizes and layout facts of a handle (all counts after normalisation). */
+typedef struct chap_info {
+    int32_t n, m, m_norm;
+    int32_t n_bin, n_int, n_cont, n_fixed;
+    int64_t nnz, nnz_int_rows, nnz_fp_rows;
+    int64_t bytes_per_pass;   /* algorithmic bytes one best-shift pass reads/writes */
+    int32_t eval_blocks;      /* CTAs of one best-shift pass */
+    int32_t n_hist_cols;      /* columns on the multi-CTA histogram path */
+} chap_info;
+
+CHAP_API void chap_options_default(chap_options *opts);
+
+/*
+ * Validate the problem, normalise its rows and copy everything to device
+ * memory owned by the handle, then set the state to x0 = clamp(0, l, u), unit
+ * weights, no tabu, iteration 0.  opts may be NULL (defaults).  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Returns CHAP_E_INVALID for
+ * inconsistent CSR/CSC, unsorted or out-of-range indices, NaN or infinite
+ * coefficients or rhs, l > u, binary bounds outside {0,1}, fractional integer
+ * bounds; CHAP_E_UNSUPPORTED when more than 2^31 - 1 nonzeros or rows, or a
+ * continuous column whose breakpoint list cannot be sorted on chip.
+ * Ref: Sec. 3.1 (problem form, normalisation), Algorithm 1 (inputs).
+ */
+CHAP_API chap_status chap_bs_create(const chap_problem *prob, const chap_options *opts,
+                                    void *stream, struct chap_bs **out);
+
+/* Free every device and host resource of the handle (NULL is accepted). */
+CHAP_API chap_status chap_bs_destroy(struct chap_bs *h);
+
+CHAP_API chap_status chap_bs_info(const struct chap_bs *h, chap_info *info);
+
+/*
+ * Set the assignment and weights, reset tabu stamps and the iteration counter
+ * to 0, recompute every residual from scratch (row sums in CSR order) and set
+ * best_nviol = nviol.  x[n] may be NULL (x0); w[m_norm] may be NULL (all 1).
+ * x must lie in the bounds and be integral on binary/integer variables;
+ * weights must be >= 1.  mem: CHAP_MEM_HOST or CHAP_MEM_DEVICE for x and w.
+ */
+CHAP_API chap_status chap_bs_set_state(struct chap_bs *h, const double *x, const int32_t *w, int32_t mem);
+
+/*
+ * Full checkpoint restore: like chap_bs_set_state, plus the tabu stamps
+ * tabu_inc[n] / tabu_dec[n] (an increase / decrease of x_j is tabu while
+ * iter < stamp), the iteration counter and best_nviol.  Host memory.
+ */
+CHAP_API chap_status chap_bs_set_checkpoint(struct chap_bs *h, const double *x, const int32_t *w,
+                                            const int64_t *tabu_inc, const int64_t *tabu_dec,
+                                            int64_t iter, int64_t best_nviol);
+
+/*
+ * Read the state back.  Any pointer may be NULL.  x[n], w[m_norm],
+ * tabu_inc[n], tabu_dec[n] in `mem` memory; scalars[4] = {iter, nviol,
+ * best_nviol, feasible_iter} always host.  Synchronises the stream when any
+ * host output is requested.
+ */
+CHAP_API chap_status chap_bs_get_state(struct chap_bs *h, double *x, int32_t *w, int64_t *tabu_inc,
+                                       int64_t *tabu_dec, int64_t *scalars, int32_t mem);
+
+/*
+ * Residuals r = a.x - b of the normalised rows as doubles (exact on integral
+ * rows), r[m_norm] in `mem` memory.
+ */
+CHAP_API chap_status chap_bs_residuals(struct chap_bs *h, double *r, int32_t mem);
+
+/*
+ * One best-shift pass at the current state (Sec. 3.1 "Best Shift Moves",
+ * Algorithm 1; binary variables: the flip): for every variable j the
+ * admissible value with the largest score, ties broken by the smallest
+ * |x - xbar_j| and then the smaller x; (xbar_j, 0, 0) when no admissible value
+ * has a positive score.  Candidates are the finite bounds and the breakpoints.
+ * Admissible: not tabu at the current iteration, or nviol + dnviol < best_nviol
+ * (aspiration).  Outputs, each optional (NULL): xhat[n], score_half[n],
+ * dnviol[n] in `mem` memory; best (host) = the move of the largest score, ties
+ * broken by the lowest variable index, var = -1 when no score is positive.
+ */
+CHAP_API chap_status chap_bs_best_shift(struct chap_bs *h, double *xhat, int64_t *score_half,
+                                        int32_t *dnviol, chap_move *best, int32_t mem);
+
+/*
+ * Apply one move x_var <- new_value with the incremental residual update
+ * r_i += a_ij (new - old) on the rows of column var (Sec. 3.1, "Memory
+ * Considerations", first point), stamp the reverse direction tabu for
+ * `tenure` iterations and advance the iteration counter.  var = -1 instead adds
+ * 1 to the weight of every violated normalised row (and advances the counter).
+ * new_value must be in the domain of var and differ from its current value.
+ */
+CHAP_API chap_status chap_bs_apply(struct chap_bs *h, int32_t var, double new_value);
+
+/* One full tabu iteration: best-shift pass, selection, then apply or weight update.
+ * out (host, optional) receives the move taken. */
+CHAP_API chap_status chap_bs_step(struct chap_bs *h, chap_move *out);
+
+/*
+ * Run the tabu search from the current state: iterations are recorded into a
+ * CUDA graph of opts->graph_iters iterations (Sec. 3.1, "Kernel
+ * Specialization", last point) and replayed until no row is violated (when
+ * stop_at_feasible) or opts->max_iters iterations have run in this call.
+ * opts may be NULL (the create options).  result (host) is filled on success.
+ */
+CHAP_API chap_status chap_tabu_run(struct chap_bs *h, const chap_options *opts, chap_tabu_result *result);
+
+CHAP_API const char *chap_status_str(chap_status s);
+CHAP_API const char *chap_last_error(const struct chap_bs *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHAP_H */

@@ -28,12 +28,15 @@
  *    Scores are returned in half-weight units (an int64 "s_half" = 2 s).
  *
  *  - Best shift (Eq. best_move) over the candidate set of Sec. 3.1: the finite
- *    bounds l_j, u_j and every breakpoint t_ij = (b_i - sum_{k!=j} a_ik xbar_k)
- *    / a_ij lying in [l_j, u_j], rounded down when a_ij > 0 and up when
- *    a_ij < 0 for integer variables (Algorithm 1, breakpoint step).  A row that
- *    is satisfied with |r| <= eps is "tight": its breakpoint is xbar_j itself,
- *    which is never a candidate.  Binary variables have the single flip
- *    candidate 1 - xbar_j (Sec. 3.1, "Best Shift Moves").
+ *    bounds l_j, u_j and every breakpoint lying in [l_j, u_j].  For a continuous
+ *    variable the breakpoint is t_ij = (b_i - sum_{k!=j} a_ik xbar_k) / a_ij;
+ *    a row that is satisfied with |r| <= eps is "tight" and its breakpoint is
+ *    xbar_j itself, which is never a candidate.  For an integer variable it is
+ *    the same quotient with b_i replaced by b_i + eps, rounded down when
+ *    a_ij > 0 and up when a_ij < 0 (Algorithm 1, breakpoint step): the last
+ *    integer at which the row is still satisfied within the tolerance (eps = 0
+ *    on integral rows gives the paper's formula unchanged).  Binary variables
+ *    have the single flip candidate 1 - xbar_j (Sec. 3.1, "Best Shift Moves").
  *
  *  - Tabu and aspiration (the framework the paper builds on; its rules are not
  *    restated there, the reading used here is): after a move at iteration k
@@ -298,11 +301,17 @@ static void best_shift_var(const orc_t *h, int32_t j, const double *x, const int
                 int32_t k = h->first_nr[i] + q;
                 double a_j;
                 double rest = activity_without(h, k, x, j, &a_j);
-                double r = activity(h, k, x) - h->nr_rhs[k];
-                int viol = r > h->nr_eps[k];
-                if (!viol && fabs(r) <= h->nr_eps[k]) continue; /* tight: breakpoint is xbar */
-                double t = (h->nr_rhs[k] - rest) / a_j;
-                if (h->vtype[j] == ORC_INT) t = (a_j > 0.0) ? floor(t) : ceil(t);
+                double t;
+                if (h->vtype[j] == ORC_INT) {
+                    double bt = h->nr_rhs[k] + h->nr_eps[k];
+                    t = (bt - rest) / a_j;
+                    t = (a_j > 0.0) ? floor(t) : ceil(t);
+                } else {
+                    double r = activity(h, k, x) - h->nr_rhs[k];
+                    int viol = r > h->nr_eps[k];
+                    if (!viol && fabs(r) <= h->nr_eps[k]) continue; /* tight: breakpoint is xbar */
+                    t = (h->nr_rhs[k] - rest) / a_j;
+                }
                 eval_candidate(h, j, t, x, w, tabu_inc, tabu_dec, iter, nviol, best_nviol, &best);
             }
         }

@@ -128,13 +128,15 @@ def candidate_values(prob, x, j, feas_tol=0.0):
     for coeffs, b, eps in rows:
         if j not in coeffs:
             continue
-        r = activity(coeffs, xf) - b
-        if r <= eps and abs(r) <= eps:
-            continue
         rest = activity({k: a for k, a in coeffs.items() if k != j}, xf)
-        t = (b - rest) / coeffs[j]
         if prob.vtype[j] == INT:
+            t = (b + eps - rest) / coeffs[j]
             t = F(math.floor(t)) if coeffs[j] > 0 else F(math.ceil(t))
+        else:
+            r = activity(coeffs, xf) - b
+            if r <= eps and abs(r) <= eps:
+                continue
+            t = (b - rest) / coeffs[j]
         if F(float(prob.lb[j])) <= t <= F(float(prob.ub[j])):
             c.add(t)
     c.discard(xf[j])

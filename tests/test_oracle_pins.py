@@ -93,6 +93,23 @@ def test_exhaustive_integer_domains(seed, dyadic):
 
 
 @pytest.mark.parametrize("seed", range(40))
+def test_exhaustive_integer_domains_with_tolerance(seed):
+    """Non-integral rows (dyadic coefficients) with a tolerance eps = 0.25 max(1,|b|):
+    the integer breakpoints are the step points of the tolerance-aware penalty,
+    so the maximum over the whole domain is still attained at a candidate."""
+    prob = inst.gen_tiny_mixed(500 + seed, n=6, m=5, max_len=4, dom=12, cont_frac=0.0, dyadic=True)
+    rng = np.random.default_rng(1500 + seed)
+    orc = Oracle(prob, feas_tol=0.25)
+    x = prob.x0
+    w = rng.integers(1, 4, size=orc.mn).astype(np.int32)
+    ti, td = _random_tabu(rng, prob.n, 2)
+    _, _, nviol = orc.residuals(x)
+    bn = nviol - int(rng.integers(0, 2))
+    xh, sh, dc = orc.best_shift(x, w, ti, td, 2, nviol, bn)
+    _check_against_exhaustive(prob, x, w, ti, td, 2, nviol, bn, 0.25, xh, sh, dc)
+
+
+@pytest.mark.parametrize("seed", range(40))
 def test_continuous_grid_never_beats_best(seed):
     prob = inst.gen_tiny_mixed(seed, n=5, m=5, max_len=4, dom=6, cont_frac=0.5, dyadic=True)
     rng = np.random.default_rng(2000 + seed)
