@@ -1,0 +1,311 @@
+"""Benchmark of the GB300 best-shift tabu search (plain exact path).
+
+A step is one tabu iteration over the whole instance: the full best-shift pass
+(every variable's best shift, Algorithm 1 / binary flips), the selection of the
+best admissible move, and its incremental application (or a weight update).
+
+Default workload: the general-integer MIP (200k vars: 70% binary, 20% integer
+in [0,100], 10% continuous in [0,1e3]; 100k rows 40/40/20 <=/>=/=; Zipf(1.5)
+row lengths clipped to [2,5000]; half integral rows, half N(0,1) rows).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
+the library's stream, with a 256 MiB write between steps to flush L2.  Under
+torchrun every rank runs an independent replica (weak scaling); the time is the
+max over ranks.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_05086_gb300 import instances as inst  # noqa: E402
+
+METRIC = "tabu moves/s (plain exact best-shift iteration, general 200k-var MIP)"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.dev = dev_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(prob, target_s=12.0, seed=0):
+    """The oracle's best shift on a seeded sample of variables at x0, extrapolated to
+    one full pass; one pass = one tabu move, so moves/s = 1 / pass time."""
+    from oracle.oracle import Oracle, max_threads
+    orc = Oracle(prob)
+    st = orc.initial_state()
+    _, _, nv = orc.residuals(st["x"])
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(prob.n).astype(np.int32)
+    size, used, t_total, done = 64, 0, 0.0, 0
+    while t_total < target_s and used < prob.n:
+        vs = order[used:used + size]
+        t0 = time.perf_counter()
+        orc.best_shift(st["x"], st["w"], st["tabu_inc"], st["tabu_dec"], 0, nv, nv, vars=vs)
+        t_total += time.perf_counter() - t0
+        used += len(vs)
+        done += len(vs)
+        size *= 2
+    pass_s = t_total * prob.n / done
+    return {"value": 1.0 / pass_s, "unit": "moves/s", "cores": max_threads(), "kind": "oracle",
+            "sample": f"oracle best shift of {done} of {prob.n} variables at x0 "
+                      f"({t_total:.1f} s), extrapolated to one full pass per move"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    prob = inst.make(args.workload)
+    from oracle.oracle import Oracle, max_threads
+    orc = Oracle(prob)
+    st = orc.initial_state()
+    _, _, nv = orc.residuals(st["x"])
+    rng = np.random.default_rng(1)
+    sample = args.ref_sample
+    times = []
+    for k in range(args.warmup + args.steps):
+        vs = rng.choice(prob.n, size=sample, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        orc.best_shift(st["x"], st["w"], st["tabu_inc"], st["tabu_dec"], 0, nv, nv, vars=vs)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt * prob.n / sample)
+    pass_s = float(np.mean(times))
+    value = 1.0 / pass_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": pass_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": prob.n, "m": prob.m, "nnz": prob.nnz},
+        "cpu_baseline": {"value": value, "unit": "moves/s", "cores": max_threads(), "kind": "oracle",
+                         "sample": f"each step: oracle best shift of {sample} random variables at x0, "
+                                   f"extrapolated to all {prob.n}"},
+        "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="general_200k", choices=sorted(inst.WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph-iters", type=int, default=2000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2605_05086_gb300 import chap
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+
+    prob = inst.make(args.workload)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(prob, target_s=args.cpu_seconds)
+
+    bs = chap.BestShift(prob, stream=stream.cuda_stream, tenure=10)
+    info = bs.info
+    lib = chap.load()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        st = lib.chap_bs_step(bs.h, None)
+        if st != 0:
+            raise RuntimeError(lib.chap_last_error(bs.h).decode())
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    st0 = bs.state()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(dev_index)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) * 1e-3
+    st1 = bs.state()
+    moves = st1["moves"] - st0["moves"]
+    iters = st1["iter"] - st0["iter"]
+
+    # best-shift pass alone (the dominant kernels): eval + selection, L2 flushed
+    npass = min(args.steps, 100)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(npass)]
+    for k in range(npass):
+        flush.zero_()
+        pev[k][0].record(stream)
+        s = lib.chap_bs_best_shift(bs.h, None, None, None, None, chap.CHAP_MEM_DEVICE)
+        pev[k][1].record(stream)
+        if s != 0:
+            raise RuntimeError(lib.chap_last_error(bs.h).decode())
+    torch.cuda.synchronize()
+    pass_ms = float(np.mean([a.elapsed_time(b) for a, b in pev]))
+
+    # production loop: CUDA-graph replay of back-to-back iterations (L2 warm)
+    res = bs.run(max_iters=args.graph_iters, stop_at_feasible=0, graph_iters=64)
+
+    # end to end through the C ABI with host buffers: set the start point from
+    # host memory, run 64 graph iterations, read the result back
+    e2e_steps = 5
+    xs = bs.state()["x"]
+    t0 = time.perf_counter()
+    e2e_moves = 0
+    for _ in range(e2e_steps):
+        bs.set_state(xs)
+        r = bs.run(max_iters=64, stop_at_feasible=0, graph_iters=64)
+        e2e_moves += r.moves
+    e2e_s = time.perf_counter() - t0
+
+    t_max = total_s
+    moves_all = moves
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        mv = torch.tensor([float(moves)], device="cuda")
+        dist.all_reduce(mv)
+        moves_all = int(mv.item())
+    if rank == 0:
+        peak, peak_kind = peaks()
+        achieved = info.bytes_per_pass / (pass_ms * 1e-3) / 1e9
+        line = {
+            "metric": METRIC,
+            "value": moves_all / t_max,
+            "unit": "moves/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_max * 1e3 / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int64+f64",
+            "data": "synthetic",
+            "config": {
+                "workload": args.workload, "n": prob.n, "m": prob.m, "m_norm": info.m_norm, "nnz": prob.nnz,
+                "n_bin": info.n_bin, "n_int": info.n_int, "n_cont": info.n_cont, "tenure": 10,
+                "l2": "flushed between timed steps (256 MiB write)",
+                "iters_per_s": iters / total_s, "moves_in_timed_steps": moves, "iters_in_timed_steps": iters,
+                "replicas": "independent per rank" if world > 1 else "single",
+                "graph_warm": {"iters": res.iters, "moves": res.moves, "seconds": res.seconds,
+                               "moves_per_s": res.moves / res.seconds if res.seconds > 0 else None,
+                               "final_nviol": res.final_nviol, "best_nviol": res.best_nviol},
+            },
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "best-shift pass (eval kernels + selection)",
+                         "bytes_per_launch": info.bytes_per_pass, "ms_per_launch": pass_ms,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_moves / e2e_s, "unit": "moves/s",
+                    "h2d_bytes_per_step": 8 * prob.n + 16 * prob.m,
+                    "d2h_bytes_per_step": 8 * prob.n + 256 * 4,
+                    "call": "chap_bs_set_state(host x) + chap_tabu_run(64 graph iterations) + result to host"},
+            "gpu_launches": info.launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    bs.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

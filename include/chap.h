@@ -134,6 +134,8 @@ typedef struct chap_info {
     int64_t bytes_per_pass;   /* algorithmic bytes one best-shift pass reads/writes */
     int32_t eval_blocks;      /* CTAs of one best-shift pass */
     int32_t n_hist_cols;      /* columns on the multi-CTA histogram path */
+    int32_t launches_per_step;/* kernel launches of one tabu iteration (chap_bs_step) */
+    int32_t reserved[7];
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);
@@ -177,9 +179,10 @@ CHAP_API chap_status chap_bs_set_checkpoint(struct chap_bs *h, const double *x, 
 
 /*
  * Read the state back.  Any pointer may be NULL.  x[n], w[m_norm],
- * tabu_inc[n], tabu_dec[n] in `mem` memory; scalars[4] = {iter, nviol,
- * best_nviol, feasible_iter} always host.  Synchronises the stream when any
- * host output is requested.
+ * tabu_inc[n], tabu_dec[n] in `mem` memory; scalars[6] = {iter, nviol,
+ * best_nviol, feasible_iter, moves, weight_updates} always host, the last two
+ * counted since the last chap_bs_set_state / chap_bs_set_checkpoint.
+ * Synchronises the stream when any host output is requested.
  */
 CHAP_API chap_status chap_bs_get_state(struct chap_bs *h, double *x, int32_t *w, int64_t *tabu_inc,
                                        int64_t *tabu_dec, int64_t *scalars, int32_t mem);

@@ -280,7 +280,15 @@ static void eval_candidate(const orc_t *h, int32_t j, double c, const double *x,
     if (admissible) consider(best, xbar, c, s, dc);
 }
 
-/* Best shift of one variable (Eq. best_move on the candidate set above). */
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Best shift of one variable (Eq. best_move on the candidate set above): the
+ * candidate values are collected, sorted and deduplicated, then each distinct
+ * value is scored from scratch. */
 static void best_shift_var(const orc_t *h, int32_t j, const double *x, const int32_t *w,
                            const int64_t *tabu_inc, const int64_t *tabu_dec, int64_t iter,
                            int64_t nviol, int64_t best_nviol,
@@ -291,29 +299,38 @@ static void best_shift_var(const orc_t *h, int32_t j, const double *x, const int
     if (h->vtype[j] == ORC_BIN) {
         eval_candidate(h, j, 1.0 - xbar, x, w, tabu_inc, tabu_dec, iter, nviol, best_nviol, &best);
     } else {
-        if (isfinite(h->lb[j]))
-            eval_candidate(h, j, h->lb[j], x, w, tabu_inc, tabu_dec, iter, nviol, best_nviol, &best);
-        if (isfinite(h->ub[j]))
-            eval_candidate(h, j, h->ub[j], x, w, tabu_inc, tabu_dec, iter, nviol, best_nviol, &best);
-        for (int64_t e = h->col_ptr[j]; e < h->col_ptr[j + 1]; ++e) {
-            int32_t i = h->row_idx[e];
-            for (int32_t q = 0; q < h->num_nr[i]; ++q) {
-                int32_t k = h->first_nr[i] + q;
-                double a_j;
-                double rest = activity_without(h, k, x, j, &a_j);
-                double t;
-                if (h->vtype[j] == ORC_INT) {
-                    double bt = h->nr_rhs[k] + h->nr_eps[k];
-                    t = (bt - rest) / a_j;
-                    t = (a_j > 0.0) ? floor(t) : ceil(t);
-                } else {
-                    double r = activity(h, k, x) - h->nr_rhs[k];
-                    int viol = r > h->nr_eps[k];
-                    if (!viol && fabs(r) <= h->nr_eps[k]) continue; /* tight: breakpoint is xbar */
-                    t = (h->nr_rhs[k] - rest) / a_j;
+        int64_t len = h->col_ptr[j + 1] - h->col_ptr[j];
+        double *cand = (double *)malloc(sizeof(double) * (size_t)(4 * len + 2));
+        int64_t nc = 0;
+        if (cand) {
+            if (isfinite(h->lb[j])) cand[nc++] = h->lb[j];
+            if (isfinite(h->ub[j])) cand[nc++] = h->ub[j];
+            for (int64_t e = h->col_ptr[j]; e < h->col_ptr[j + 1]; ++e) {
+                int32_t i = h->row_idx[e];
+                for (int32_t q = 0; q < h->num_nr[i]; ++q) {
+                    int32_t k = h->first_nr[i] + q;
+                    double a_j;
+                    double rest = activity_without(h, k, x, j, &a_j);
+                    double t;
+                    if (h->vtype[j] == ORC_INT) {
+                        double bt = h->nr_rhs[k] + h->nr_eps[k];
+                        t = (bt - rest) / a_j;
+                        t = (a_j > 0.0) ? floor(t) : ceil(t);
+                    } else {
+                        double r = activity(h, k, x) - h->nr_rhs[k];
+                        int viol = r > h->nr_eps[k];
+                        if (!viol && fabs(r) <= h->nr_eps[k]) continue; /* tight: breakpoint is xbar */
+                        t = (h->nr_rhs[k] - rest) / a_j;
+                    }
+                    cand[nc++] = t + 0.0;
                 }
-                eval_candidate(h, j, t, x, w, tabu_inc, tabu_dec, iter, nviol, best_nviol, &best);
             }
+            qsort(cand, (size_t)nc, sizeof(double), cmp_double);
+            for (int64_t q = 0; q < nc; ++q) {
+                if (q > 0 && cand[q] == cand[q - 1]) continue;
+                eval_candidate(h, j, cand[q], x, w, tabu_inc, tabu_dec, iter, nviol, best_nviol, &best);
+            }
+            free(cand);
         }
     }
     if (best.have && best.s > 0) {

@@ -1,0 +1,277 @@
+"""Python binding of libchap.so (include/chap.h): argument marshalling only.
+
+Every step of the best-shift tabu search runs in the library's CUDA kernels;
+this module converts numpy arrays / torch CUDA tensors to pointers and status
+codes to exceptions.  There is no CPU fallback: when the library is missing or
+no GPU is present, loading fails with an exception.
+
+Function names follow the C ABI (chap_bs_create, chap_bs_best_shift,
+chap_bs_apply, chap_tabu_run, ...); the BestShift class is a thin handle wrapper.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CHAP_OK, CHAP_E_INVALID, CHAP_E_OOM, CHAP_E_CUDA, CHAP_E_TIMEOUT, CHAP_E_STATE, CHAP_E_UNSUPPORTED = range(7)
+CHAP_MEM_HOST, CHAP_MEM_DEVICE = 0, 1
+
+EXPORTED = [
+    "chap_options_default", "chap_bs_create", "chap_bs_destroy", "chap_bs_info", "chap_bs_set_state",
+    "chap_bs_set_checkpoint", "chap_bs_get_state", "chap_bs_residuals", "chap_bs_best_shift",
+    "chap_bs_apply", "chap_bs_step", "chap_tabu_run", "chap_status_str", "chap_last_error",
+]
+
+
+class ChapError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class chap_problem(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("row_val", C.c_void_p),
+                ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p), ("col_val", C.c_void_p),
+                ("lb", C.c_void_p), ("ub", C.c_void_p), ("obj", C.c_void_p), ("rhs", C.c_void_p),
+                ("vtype", C.c_void_p), ("sense", C.c_void_p)]
+
+
+class chap_options(C.Structure):
+    _fields_ = [("feas_tol", C.c_double), ("tenure", C.c_int32), ("graph_iters", C.c_int32),
+                ("max_iters", C.c_int64), ("stop_at_feasible", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class chap_move(C.Structure):
+    _fields_ = [("var", C.c_int32), ("dnviol", C.c_int32), ("score_half", C.c_int64),
+                ("old_value", C.c_double), ("new_value", C.c_double)]
+
+
+class chap_tabu_result(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("moves", C.c_int64), ("feasible_iter", C.c_int64),
+                ("final_nviol", C.c_int64), ("best_nviol", C.c_int64), ("seconds", C.c_double),
+                ("time_to_feasible_s", C.c_double), ("objective", C.c_double)]
+
+
+class chap_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("m_norm", C.c_int32),
+                ("n_bin", C.c_int32), ("n_int", C.c_int32), ("n_cont", C.c_int32), ("n_fixed", C.c_int32),
+                ("nnz", C.c_int64), ("nnz_int_rows", C.c_int64), ("nnz_fp_rows", C.c_int64),
+                ("bytes_per_pass", C.c_int64), ("eval_blocks", C.c_int32), ("n_hist_cols", C.c_int32),
+                ("launches_per_step", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libchap.so (building it first when missing).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is missing; build it with paper_2605_05086_gb300.build.build()")
+        _build.build()
+    lib = C.CDLL(_build.LIB)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "chap_options_default": (None, [P]),
+        "chap_bs_create": (I32, [P, P, P, P]),
+        "chap_bs_destroy": (I32, [P]),
+        "chap_bs_info": (I32, [P, P]),
+        "chap_bs_set_state": (I32, [P, P, P, I32]),
+        "chap_bs_set_checkpoint": (I32, [P, P, P, P, P, I64, I64]),
+        "chap_bs_get_state": (I32, [P, P, P, P, P, P, I32]),
+        "chap_bs_residuals": (I32, [P, P, I32]),
+        "chap_bs_best_shift": (I32, [P, P, P, P, P, I32]),
+        "chap_bs_apply": (I32, [P, I32, D]),
+        "chap_bs_step": (I32, [P, P]),
+        "chap_tabu_run": (I32, [P, P, P]),
+        "chap_status_str": (C.c_char_p, [I32]),
+        "chap_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(h, status):
+    if status != CHAP_OK:
+        lib = load()
+        msg = lib.chap_last_error(h).decode() if h else lib.chap_status_str(status).decode()
+        raise ChapError(status, msg or lib.chap_status_str(status).decode())
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return C.c_void_p(0)
+
+
+def chap_options_default() -> chap_options:
+    o = chap_options()
+    load().chap_options_default(C.byref(o))
+    return o
+
+
+def chap_bs_create(prob, opts: chap_options | None = None, stream=None):
+    """Create a handle over a Problem (instances.Problem-like, host numpy arrays)."""
+    lib = load()
+    keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
+        (prob.row_ptr, np.int64), (prob.col_idx, np.int32), (prob.row_val, np.float64),
+        (prob.col_ptr, np.int64), (prob.row_idx, np.int32), (prob.col_val, np.float64),
+        (prob.lb, np.float64), (prob.ub, np.float64), (prob.obj, np.float64), (prob.rhs, np.float64),
+        (prob.vtype, np.uint8), (prob.sense, np.uint8))]
+    p = chap_problem(prob.n, prob.m, int(prob.row_ptr[-1]), *[_ptr(a) for a in keep])
+    h = C.c_void_p()
+    st = lib.chap_bs_create(C.byref(p), None if opts is None else C.byref(opts), _stream(stream), C.byref(h))
+    if st != CHAP_OK:
+        raise ChapError(st, "chap_bs_create: " + lib.chap_status_str(st).decode())
+    return h
+
+
+def chap_bs_destroy(h):
+    _check(None, load().chap_bs_destroy(h))
+
+
+def chap_bs_info(h) -> chap_info:
+    inf = chap_info()
+    _check(h, load().chap_bs_info(h, C.byref(inf)))
+    return inf
+
+
+def chap_bs_set_state(h, x=None, w=None, mem=CHAP_MEM_HOST):
+    if mem == CHAP_MEM_HOST:
+        x = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        w = None if w is None else np.ascontiguousarray(w, dtype=np.int32)
+    _check(h, load().chap_bs_set_state(h, _ptr(x), _ptr(w), mem))
+
+
+def chap_bs_set_checkpoint(h, x, w, tabu_inc, tabu_dec, it, best_nviol):
+    arrs = [np.ascontiguousarray(x, np.float64), np.ascontiguousarray(w, np.int32),
+            np.ascontiguousarray(tabu_inc, np.int64), np.ascontiguousarray(tabu_dec, np.int64)]
+    _check(h, load().chap_bs_set_checkpoint(h, *[_ptr(a) for a in arrs], int(it), int(best_nviol)))
+
+
+def chap_bs_get_state(h, n, m_norm):
+    """Host copies of x, w, tabu stamps and the scalars (iter, nviol, best_nviol,
+    feasible_iter, moves, weight_updates)."""
+    x = np.zeros(n)
+    w = np.zeros(m_norm, np.int32)
+    ti = np.zeros(n, np.int64)
+    td = np.zeros(n, np.int64)
+    sc = np.zeros(6, np.int64)
+    _check(h, load().chap_bs_get_state(h, _ptr(x), _ptr(w), _ptr(ti), _ptr(td), _ptr(sc), CHAP_MEM_HOST))
+    return dict(x=x, w=w, tabu_inc=ti, tabu_dec=td, iter=int(sc[0]), nviol=int(sc[1]),
+                best_nviol=int(sc[2]), feasible_iter=int(sc[3]), moves=int(sc[4]), weight_updates=int(sc[5]))
+
+
+def chap_bs_residuals(h, m_norm, out=None, mem=CHAP_MEM_HOST):
+    r = np.zeros(m_norm) if out is None else out
+    _check(h, load().chap_bs_residuals(h, _ptr(r), mem))
+    return r
+
+
+def chap_bs_best_shift(h, n=None, xhat=None, score_half=None, dnviol=None, mem=CHAP_MEM_HOST, want_vars=True):
+    """Best-shift pass.  With mem=HOST and want_vars, returns numpy (xhat, score_half, dnviol, move)."""
+    if mem == CHAP_MEM_HOST and want_vars and xhat is None:
+        xhat = np.zeros(n)
+        score_half = np.zeros(n, np.int64)
+        dnviol = np.zeros(n, np.int32)
+    mv = chap_move()
+    _check(h, load().chap_bs_best_shift(h, _ptr(xhat), _ptr(score_half), _ptr(dnviol), C.byref(mv), mem))
+    return xhat, score_half, dnviol, mv
+
+
+def chap_bs_apply(h, var, new_value):
+    _check(h, load().chap_bs_apply(h, int(var), float(new_value)))
+
+
+def chap_bs_step(h, want_move=True):
+    mv = chap_move()
+    _check(h, load().chap_bs_step(h, C.byref(mv) if want_move else None))
+    return mv
+
+
+def chap_tabu_run(h, opts: chap_options | None = None) -> chap_tabu_result:
+    res = chap_tabu_result()
+    _check(h, load().chap_tabu_run(h, None if opts is None else C.byref(opts), C.byref(res)))
+    return res
+
+
+class BestShift:
+    """Handle wrapper: BestShift(problem, tenure=10, feas_tol=1e-9, ...)."""
+
+    def __init__(self, prob, stream=None, **opts):
+        o = chap_options_default()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.opts = o
+        self.h = chap_bs_create(prob, o, stream)
+        self.info = chap_bs_info(self.h)
+        self.n, self.m_norm = prob.n, self.info.m_norm
+
+    def close(self):
+        if getattr(self, "h", None):
+            chap_bs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, x=None, w=None, mem=CHAP_MEM_HOST):
+        chap_bs_set_state(self.h, x, w, mem)
+
+    def set_checkpoint(self, st):
+        chap_bs_set_checkpoint(self.h, st["x"], st["w"], st["tabu_inc"], st["tabu_dec"], st["iter"], st["best_nviol"])
+
+    def state(self):
+        return chap_bs_get_state(self.h, self.n, self.m_norm)
+
+    def residuals(self):
+        return chap_bs_residuals(self.h, self.m_norm)
+
+    def best_shift(self):
+        return chap_bs_best_shift(self.h, self.n)
+
+    def apply(self, var, value):
+        chap_bs_apply(self.h, var, value)
+
+    def step(self):
+        return chap_bs_step(self.h)
+
+    def run(self, **kw):
+        o = chap_options()
+        C.memmove(C.byref(o), C.byref(self.opts), C.sizeof(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return chap_tabu_run(self.h, o)

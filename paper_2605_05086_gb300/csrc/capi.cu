@@ -1,0 +1,769 @@
+// Host side of the C ABI declared in include/chap.h: validation, row
+// normalisation (Sec. 3.1, "Memory Considerations"), the split CSC store,
+// work tiles of the best-shift pass, state handling and the CUDA-graph driver
+// of the tabu loop (Sec. 3.1, "Kernel Specialization", last point).
+#include "../../include/chap.h"
+#include "chap_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace chap {
+cudaError_t setup_kernel_attributes(int cta_smem, int hist_smem);
+cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
+cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st);
+cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
+}  // namespace chap
+
+using namespace chap;
+
+struct chap_bs {
+    cudaStream_t st = nullptr;
+    cudaStream_t cap_st = nullptr;
+    chap_options opt{};
+    chap_info info{};
+    int n = 0, m = 0, m_norm = 0;
+    std::vector<double> lb, ub, obj;
+    std::vector<uint8_t> vtype, row_eq;
+    std::vector<int> nrow_base;
+    std::vector<void *> allocs;
+    Dev dev{};
+    LaunchPlan plan{};
+    // device scratch for host-memory outputs
+    double *t_xhat = nullptr;
+    long long *t_s = nullptr;
+    int *t_dc = nullptr;
+    int *t_w = nullptr;
+    double *t_r = nullptr;
+    long long *t_tabu = nullptr;
+    Ctl *h_ctl = nullptr;  // pinned
+    cudaGraphExec_t gexec = nullptr;
+    int g_iters = 0;
+    bool broken = false;
+    std::string err;
+};
+
+namespace {
+
+const double kLim52 = 4503599627370496.0;
+
+bool is_int_value(double v) { return std::isfinite(v) && std::floor(v) == v; }
+
+chap_status fail(chap_bs *h, chap_status s, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return s;
+}
+
+chap_status cuda_fail(chap_bs *h, cudaError_t e, const char *what)
+{
+    if (h) {
+        h->err = std::string(what) + ": " + cudaGetErrorString(e);
+        if (e == cudaErrorIllegalAddress || e == cudaErrorLaunchFailure || e == cudaErrorIllegalInstruction ||
+            e == cudaErrorMisalignedAddress || e == cudaErrorHardwareStackError)
+            h->broken = true;
+    }
+    return CHAP_E_CUDA;
+}
+
+#define CK(h, call, what)                                  \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, what); \
+    } while (0)
+
+template <class T>
+T *dalloc(chap_bs *h, size_t count)
+{
+    void *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    h->allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+
+template <class T>
+cudaError_t h2d(T *dst, const T *src, size_t count, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+chap_status validate(const chap_problem *p, std::string &msg)
+{
+    if (!p) { msg = "problem is NULL"; return CHAP_E_INVALID; }
+    if (p->n < 0 || p->m < 0 || p->nnz < 0) { msg = "negative size"; return CHAP_E_INVALID; }
+    if (p->nnz > (int64_t)INT_MAX - 1) { msg = "more than 2^31-1 nonzeros"; return CHAP_E_UNSUPPORTED; }
+    const int n = p->n, m = p->m;
+    const int64_t nnz = p->nnz;
+    if (!p->row_ptr || !p->col_ptr) { msg = "row_ptr/col_ptr is NULL"; return CHAP_E_INVALID; }
+    if (nnz > 0 && (!p->col_idx || !p->row_val || !p->row_idx || !p->col_val)) { msg = "index/value array is NULL"; return CHAP_E_INVALID; }
+    if (n > 0 && (!p->lb || !p->ub || !p->vtype)) { msg = "variable array is NULL"; return CHAP_E_INVALID; }
+    if (m > 0 && (!p->rhs || !p->sense)) { msg = "row array is NULL"; return CHAP_E_INVALID; }
+    if (p->row_ptr[0] != 0 || p->row_ptr[m] != nnz) { msg = "row_ptr does not span [0, nnz]"; return CHAP_E_INVALID; }
+    if (p->col_ptr[0] != 0 || p->col_ptr[n] != nnz) { msg = "col_ptr does not span [0, nnz]"; return CHAP_E_INVALID; }
+    for (int i = 0; i < m; ++i) {
+        if (p->row_ptr[i + 1] < p->row_ptr[i]) { msg = "row_ptr decreases at row " + std::to_string(i); return CHAP_E_INVALID; }
+        for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e) {
+            int j = p->col_idx[e];
+            if (j < 0 || j >= n) { msg = "column index out of range in row " + std::to_string(i); return CHAP_E_INVALID; }
+            if (e > p->row_ptr[i] && p->col_idx[e - 1] >= j) { msg = "column indices not strictly increasing in row " + std::to_string(i); return CHAP_E_INVALID; }
+            double a = p->row_val[e];
+            if (!std::isfinite(a) || a == 0.0) { msg = "zero, NaN or infinite coefficient in row " + std::to_string(i); return CHAP_E_INVALID; }
+        }
+        if (!std::isfinite(p->rhs[i])) { msg = "non-finite rhs in row " + std::to_string(i); return CHAP_E_INVALID; }
+        if (p->sense[i] > CHAP_ROW_EQ) { msg = "bad sense in row " + std::to_string(i); return CHAP_E_INVALID; }
+    }
+    std::vector<int64_t> cur(p->row_ptr, p->row_ptr + m);
+    for (int j = 0; j < n; ++j) {
+        if (p->col_ptr[j + 1] < p->col_ptr[j]) { msg = "col_ptr decreases at column " + std::to_string(j); return CHAP_E_INVALID; }
+        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) {
+            int i = p->row_idx[e];
+            if (i < 0 || i >= m) { msg = "row index out of range in column " + std::to_string(j); return CHAP_E_INVALID; }
+            if (e > p->col_ptr[j] && p->row_idx[e - 1] >= i) { msg = "row indices not strictly increasing in column " + std::to_string(j); return CHAP_E_INVALID; }
+            int64_t c = cur[i];
+            if (c >= p->row_ptr[i + 1] || p->col_idx[c] != j || p->row_val[c] != p->col_val[e]) {
+                msg = "CSC is not the transpose of CSR at column " + std::to_string(j); return CHAP_E_INVALID;
+            }
+            cur[i] = c + 1;
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        if (cur[i] != p->row_ptr[i + 1]) { msg = "CSC is not the transpose of CSR at row " + std::to_string(i); return CHAP_E_INVALID; }
+    for (int j = 0; j < n; ++j) {
+        double l = p->lb[j], u = p->ub[j];
+        if (std::isnan(l) || std::isnan(u) || l > u || l == INFINITY || u == -INFINITY) { msg = "bad bounds of variable " + std::to_string(j); return CHAP_E_INVALID; }
+        int t = p->vtype[j];
+        if (t > CHAP_VAR_CONT) { msg = "bad type of variable " + std::to_string(j); return CHAP_E_INVALID; }
+        if (t == CHAP_VAR_BIN && !((l == 0.0 || l == 1.0) && (u == 0.0 || u == 1.0))) { msg = "binary bounds not in {0,1} for variable " + std::to_string(j); return CHAP_E_INVALID; }
+        if (t == CHAP_VAR_INT && ((std::isfinite(l) && !is_int_value(l)) || (std::isfinite(u) && !is_int_value(u)))) { msg = "fractional integer bound of variable " + std::to_string(j); return CHAP_E_INVALID; }
+        if (p->obj && !std::isfinite(p->obj[j])) { msg = "non-finite objective of variable " + std::to_string(j); return CHAP_E_INVALID; }
+    }
+    return CHAP_OK;
+}
+
+void free_all(chap_bs *h)
+{
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->h_ctl) { cudaFreeHost(h->h_ctl); h->h_ctl = nullptr; }
+    if (h->cap_st) { cudaStreamDestroy(h->cap_st); h->cap_st = nullptr; }
+}
+
+chap_status read_ctl(chap_bs *h)
+{
+    CK(h, cudaMemcpyAsync(h->h_ctl, h->dev.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st), "read control block");
+    CK(h, cudaStreamSynchronize(h->st), "synchronise");
+    return CHAP_OK;
+}
+
+chap_status check_x(chap_bs *h, const double *x)
+{
+    for (int j = 0; j < h->n; ++j) {
+        double v = x[j];
+        if (!(v >= h->lb[j] && v <= h->ub[j])) return fail(h, CHAP_E_INVALID, "x out of bounds at variable " + std::to_string(j));
+        if (h->vtype[j] != CHAP_VAR_CONT && !is_int_value(v)) return fail(h, CHAP_E_INVALID, "fractional value of integer variable " + std::to_string(j));
+    }
+    return CHAP_OK;
+}
+
+// Load x (host array) and normalised weights (host array, NULL = 1), recompute residuals.
+chap_status load_state(chap_bs *h, const double *x, const int *w, const int *tabu_inc, const int *tabu_dec,
+                       long long iter, long long best_nviol, int use_best)
+{
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    chap_status s = check_x(h, x);
+    if (s != CHAP_OK) return s;
+    std::vector<double> xc(x, x + h->n);
+    for (double &v : xc) v = v + 0.0;
+    std::vector<RowState> rs(h->m);
+    for (int i = 0; i < h->m; ++i) {
+        int k = h->nrow_base[i];
+        int w1 = w ? w[k] : 1;
+        int w2 = h->row_eq[i] ? (w ? w[k + 1] : 1) : -1;
+        if (w1 < 1 || (h->row_eq[i] && w2 < 1)) return fail(h, CHAP_E_INVALID, "weights must be >= 1");
+        rs[i] = RowState{0, w1, w2};
+    }
+    Dev &d = h->dev;
+    CK(h, h2d(d.x, xc.data(), h->n, h->st), "copy x");
+    CK(h, h2d(d.rs, rs.data(), h->m, h->st), "copy weights");
+    if (tabu_inc) {
+        CK(h, h2d(d.tabu_inc, tabu_inc, h->n, h->st), "copy tabu");
+        CK(h, h2d(d.tabu_dec, tabu_dec, h->n, h->st), "copy tabu");
+    } else {
+        CK(h, cudaMemsetAsync(d.tabu_inc, 0, sizeof(int) * (size_t)std::max(h->n, 1), h->st), "reset tabu");
+        CK(h, cudaMemsetAsync(d.tabu_dec, 0, sizeof(int) * (size_t)std::max(h->n, 1), h->st), "reset tabu");
+    }
+    CK(h, cudaMemsetAsync(&d.ctl->nviol, 0, sizeof(long long), h->st), "reset nviol");
+    if (h->m > 0) CK(h, launch_residuals(d, h->st), "residual kernel");
+    CK(h, launch_finish_set_state(d, iter, best_nviol, use_best, h->st), "finish set_state");
+    // the host arrays above are released on return: make sure the copies are done
+    CK(h, cudaStreamSynchronize(h->st), "synchronise");
+    return CHAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void chap_options_default(chap_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->feas_tol = 1e-9;
+    o->tenure = 10;
+    o->graph_iters = 64;
+    o->max_iters = 1000;
+    o->stop_at_feasible = 1;
+}
+
+const char *chap_status_str(chap_status s)
+{
+    switch (s) {
+    case CHAP_OK: return "ok";
+    case CHAP_E_INVALID: return "invalid argument";
+    case CHAP_E_OOM: return "out of memory";
+    case CHAP_E_CUDA: return "CUDA error";
+    case CHAP_E_TIMEOUT: return "device wait timed out";
+    case CHAP_E_STATE: return "invalid state";
+    case CHAP_E_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+const char *chap_last_error(const chap_bs *h) { return h ? h->err.c_str() : "NULL handle"; }
+
+chap_status chap_bs_destroy(chap_bs *h)
+{
+    if (!h) return CHAP_OK;
+    cudaStreamSynchronize(h->st);
+    free_all(h);
+    delete h;
+    return CHAP_OK;
+}
+
+chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void *stream, chap_bs **out)
+{
+    if (!out) return CHAP_E_INVALID;
+    *out = nullptr;
+    chap_bs *h = new (std::nothrow) chap_bs();
+    if (!h) return CHAP_E_OOM;
+    std::string msg;
+    chap_status vs = validate(p, msg);
+    if (vs != CHAP_OK) {
+        // report the message through a throw-away handle-less path
+        std::fprintf(stderr, "chap_bs_create: %s\n", msg.c_str());
+        delete h;
+        return vs;
+    }
+    if (opts) h->opt = *opts; else chap_options_default(&h->opt);
+    if (!(h->opt.feas_tol >= 0.0) || h->opt.tenure < 0 || h->opt.graph_iters < 1) {
+        delete h;
+        return CHAP_E_INVALID;
+    }
+    h->st = static_cast<cudaStream_t>(stream);
+    const int n = p->n, m = p->m;
+    h->n = n;
+    h->m = m;
+    h->lb.assign(p->lb, p->lb + n);
+    h->ub.assign(p->ub, p->ub + n);
+    h->obj.assign(n, 0.0);
+    if (p->obj) h->obj.assign(p->obj, p->obj + n);
+    h->vtype.assign(p->vtype, p->vtype + n);
+
+    // ---- row normalisation and integrality
+    std::vector<double> sign(m), rhs(m), eps(m);
+    std::vector<uint8_t> rint(m);
+    h->row_eq.assign(m, 0);
+    h->nrow_base.assign(m, 0);
+    int mn = 0;
+    int64_t nnz_int = 0, m_fp = 0;
+    for (int i = 0; i < m; ++i) {
+        sign[i] = p->sense[i] == CHAP_ROW_GE ? -1.0 : 1.0;
+        h->row_eq[i] = p->sense[i] == CHAP_ROW_EQ;
+        h->nrow_base[i] = mn;
+        mn += h->row_eq[i] ? 2 : 1;
+        double b = p->rhs[i];
+        bool integral = is_int_value(b) && std::fabs(b) <= kLim52;
+        double mag = std::fabs(b);
+        for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1] && integral; ++e) {
+            double a = p->row_val[e];
+            int j = p->col_idx[e];
+            if (!is_int_value(a) || std::fabs(a) > 2147483647.0) integral = false;
+            else if (p->vtype[j] == CHAP_VAR_CONT) integral = false;
+            else if (!std::isfinite(p->lb[j]) || !std::isfinite(p->ub[j])) integral = false;
+            else {
+                mag += std::fabs(a) * std::max(std::fabs(p->lb[j]), std::fabs(p->ub[j]));
+                if (!(mag <= kLim52)) integral = false;
+            }
+        }
+        rint[i] = integral ? 1 : 0;
+        rhs[i] = sign[i] * b;
+        eps[i] = integral ? 0.0 : h->opt.feas_tol * std::max(1.0, std::fabs(b));
+        if (integral) nnz_int += p->row_ptr[i + 1] - p->row_ptr[i];
+        else ++m_fp;
+    }
+    h->m_norm = mn;
+
+    // ---- split CSC (integral rows: int32 coefficients; others: double)
+    std::vector<int> ci_ptr(n + 1, 0), cf_ptr(n + 1, 0);
+    std::vector<int> ci_row, ci_val, cf_row;
+    std::vector<double> cf_val;
+    ci_row.reserve(nnz_int);
+    ci_val.reserve(nnz_int);
+    cf_row.reserve(p->nnz - nnz_int);
+    cf_val.reserve(p->nnz - nnz_int);
+    for (int j = 0; j < n; ++j) {
+        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) {
+            int i = p->row_idx[e];
+            double a = sign[i] * p->col_val[e];
+            if (rint[i]) { ci_row.push_back(i); ci_val.push_back((int)a); }
+            else { cf_row.push_back(i); cf_val.push_back(a); }
+        }
+        ci_ptr[j + 1] = (int)ci_row.size();
+        cf_ptr[j + 1] = (int)cf_row.size();
+    }
+    std::vector<double> row_val(p->nnz);
+    for (int i = 0; i < m; ++i)
+        for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e) row_val[e] = sign[i] * p->row_val[e];
+
+    // ---- classify variables and build work tiles
+    std::vector<std::vector<int>> kind_vars(T_NB_HIST + 1);
+    int n_bin = 0, n_int = 0, n_cont = 0, n_fixed = 0;
+    int max_col = 0;
+    int64_t nb_bytes_vars = 0;
+    for (int j = 0; j < n; ++j) {
+        int nI = ci_ptr[j + 1] - ci_ptr[j], nF = cf_ptr[j + 1] - cf_ptr[j];
+        int len = nI + nF;
+        max_col = std::max(max_col, len);
+        if (h->lb[j] == h->ub[j]) { ++n_fixed; continue; }
+        int t = h->vtype[j];
+        if (t == CHAP_VAR_BIN) {
+            ++n_bin;
+            int k = len <= 4 ? T_BIN_G4 : len <= 8 ? T_BIN_G8 : len <= 16 ? T_BIN_G16 : len <= 2048 ? T_BIN_G32 : T_BIN_CTA;
+            kind_vars[k].push_back(j);
+            continue;
+        }
+        (t == CHAP_VAR_INT ? n_int : n_cont)++;
+        nb_bytes_vars += 16;
+        int64_t E = (std::isfinite(h->lb[j]) ? 1 : 0) + (std::isfinite(h->ub[j]) ? 1 : 0);
+        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += h->row_eq[p->row_idx[e]] ? 4 : 2;
+        int k;
+        if (E <= 32) k = T_NB_K1;
+        else if (E <= 64) k = T_NB_K2;
+        else if (E <= 128) k = T_NB_K4;
+        else if (E <= 256) k = T_NB_K8;
+        else if (E <= kCtaMaxEntries) k = T_NB_CTA;
+        else if (t == CHAP_VAR_INT && std::isfinite(h->lb[j]) && std::isfinite(h->ub[j]) &&
+                 h->ub[j] - h->lb[j] + 1 <= kHistMaxDomain) k = T_NB_HIST;
+        else {
+            std::fprintf(stderr, "chap_bs_create: column %d has %lld breakpoint entries and no on-chip path\n", j, (long long)E);
+            delete h;
+            return CHAP_E_UNSUPPORTED;
+        }
+        kind_vars[k].push_back(j);
+    }
+    std::vector<int> var_list;
+    std::vector<Tile> tiles_small, tiles_cta, tiles_hist;
+    std::vector<HistCol> hcols;
+    int max_cta_n = 0, max_hist_d = 0;
+    int64_t hist_bins = 0;
+    for (int k = 0; k <= T_NB_HIST; ++k) {
+        const std::vector<int> &vs = kind_vars[k];
+        int base = (int)var_list.size();
+        var_list.insert(var_list.end(), vs.begin(), vs.end());
+        int cnt = (int)vs.size();
+        if (cnt == 0) continue;
+        if (k <= T_BIN_G32) {
+            int G = 4 << (k - T_BIN_G4);
+            int per = (kEvalThreads / G) * 4;
+            for (int b = 0; b < cnt; b += per) tiles_small.push_back(Tile{k, base + b, base + std::min(cnt, b + per), 0});
+        } else if (k == T_BIN_CTA) {
+            for (int b = 0; b < cnt; ++b) tiles_small.push_back(Tile{k, base + b, base + b + 1, 0});
+        } else if (k <= T_NB_K8) {
+            int per = (kEvalThreads / 32) * 2;
+            for (int b = 0; b < cnt; b += per) tiles_small.push_back(Tile{k, base + b, base + std::min(cnt, b + per), 0});
+        } else if (k == T_NB_CTA) {
+            for (int b = 0; b < cnt; ++b) {
+                int j = vs[b];
+                int64_t E = (std::isfinite(h->lb[j]) ? 1 : 0) + (std::isfinite(h->ub[j]) ? 1 : 0);
+                for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += h->row_eq[p->row_idx[e]] ? 4 : 2;
+                int N = std::max(next_pow2((int)E), kCtaThreads);
+                max_cta_n = std::max(max_cta_n, N);
+                tiles_cta.push_back(Tile{k, base + b, base + b + 1, N});
+            }
+        } else {
+            for (int b = 0; b < cnt; ++b) {
+                int j = vs[b];
+                HistCol hc{};
+                hc.var = j;
+                int D = (int)(h->ub[j] - h->lb[j]) + 1;
+                max_hist_d = std::max(max_hist_d, D);
+                hc.bin_off = hist_bins;
+                hist_bins += D;
+                hc.e_begin = 0;
+                hc.e_mid = ci_ptr[j + 1] - ci_ptr[j];
+                hc.e_end = hc.e_mid + (cf_ptr[j + 1] - cf_ptr[j]);
+                hc.nchunks = std::max(1, (hc.e_end + kHistChunk - 1) / kHistChunk);
+                int hidx = (int)hcols.size();
+                for (int c = 0; c < hc.nchunks; ++c) tiles_hist.push_back(Tile{k, hidx, hidx + 1, c});
+                hcols.push_back(hc);
+            }
+        }
+    }
+    const int n_small = (int)tiles_small.size(), n_cta = (int)tiles_cta.size();
+    for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = n_small + n_cta + (int)q;
+    const int n_bb = n_small + n_cta + (int)hcols.size();
+
+    // ---- device allocation
+    Dev &d = h->dev;
+    d.n = n;
+    d.m = m;
+    d.tenure = h->opt.tenure;
+    int *ci_ptr_d = dalloc<int>(h, n + 1), *ci_row_d = dalloc<int>(h, ci_row.size()), *ci_val_d = dalloc<int>(h, ci_val.size());
+    int *cf_ptr_d = dalloc<int>(h, n + 1), *cf_row_d = dalloc<int>(h, cf_row.size());
+    double *cf_val_d = dalloc<double>(h, cf_val.size());
+    long long *row_ptr_d = dalloc<long long>(h, m + 1);
+    int *col_idx_d = dalloc<int>(h, p->nnz);
+    double *row_val_d = dalloc<double>(h, p->nnz), *rhs_d = dalloc<double>(h, m), *eps_d = dalloc<double>(h, m);
+    unsigned char *rint_d = dalloc<unsigned char>(h, m);
+    int *nrb_d = dalloc<int>(h, m);
+    unsigned char *vt_d = dalloc<unsigned char>(h, n);
+    double *lb_d = dalloc<double>(h, n), *ub_d = dalloc<double>(h, n), *obj_d = dalloc<double>(h, n);
+    d.x = dalloc<double>(h, n);
+    d.rs = dalloc<RowState>(h, m);
+    d.tabu_inc = dalloc<int>(h, n);
+    d.tabu_dec = dalloc<int>(h, n);
+    d.ctl = dalloc<Ctl>(h, 1);
+    int *vl_d = dalloc<int>(h, var_list.size());
+    d.block_best = dalloc<Cand>(h, n_bb);
+    d.n_block_best = n_bb;
+    Tile *ts_d = dalloc<Tile>(h, tiles_small.size()), *tc_d = dalloc<Tile>(h, tiles_cta.size()), *th_d = dalloc<Tile>(h, tiles_hist.size());
+    HistCol *hc_d = dalloc<HistCol>(h, hcols.size());
+    d.hbins = dalloc<HBin>(h, hist_bins);
+    d.hacc = dalloc<HistAcc>(h, hcols.size());
+    h->t_xhat = dalloc<double>(h, n);
+    h->t_s = dalloc<long long>(h, n);
+    h->t_dc = dalloc<int>(h, n);
+    h->t_w = dalloc<int>(h, mn);
+    h->t_r = dalloc<double>(h, mn);
+    h->t_tabu = dalloc<long long>(h, n);
+    bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && row_ptr_d && col_idx_d &&
+              row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.rs &&
+              d.tabu_inc && d.tabu_dec && d.ctl && vl_d && d.block_best && ts_d && tc_d && th_d && hc_d &&
+              d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
+    if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
+    if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
+    if (!ok) {
+        free_all(h);
+        delete h;
+        return CHAP_E_OOM;
+    }
+    d.ci_ptr = ci_ptr_d; d.ci_row = ci_row_d; d.ci_val = ci_val_d;
+    d.cf_ptr = cf_ptr_d; d.cf_row = cf_row_d; d.cf_val = cf_val_d;
+    d.row_ptr = row_ptr_d; d.col_idx = col_idx_d; d.row_val = row_val_d;
+    d.rhs = rhs_d; d.eps = eps_d; d.row_int = rint_d; d.nrow_base = nrb_d;
+    d.vtype = vt_d; d.lb = lb_d; d.ub = ub_d; d.obj = obj_d;
+    d.var_list = vl_d;
+    d.hcols = hc_d;
+    cudaStream_t st = h->st;
+    std::vector<long long> rp(p->row_ptr, p->row_ptr + m + 1);
+    cudaError_t e = cudaSuccess;
+#define UP(dst, src, cnt) if (e == cudaSuccess) e = h2d(dst, src, cnt, st)
+    UP(ci_ptr_d, ci_ptr.data(), n + 1); UP(ci_row_d, ci_row.data(), ci_row.size()); UP(ci_val_d, ci_val.data(), ci_val.size());
+    UP(cf_ptr_d, cf_ptr.data(), n + 1); UP(cf_row_d, cf_row.data(), cf_row.size()); UP(cf_val_d, cf_val.data(), cf_val.size());
+    UP(row_ptr_d, rp.data(), m + 1); UP(col_idx_d, p->col_idx, p->nnz); UP(row_val_d, row_val.data(), p->nnz);
+    UP(rhs_d, rhs.data(), m); UP(eps_d, eps.data(), m); UP(rint_d, rint.data(), m); UP(nrb_d, h->nrow_base.data(), m);
+    UP(vt_d, p->vtype, n); UP(lb_d, p->lb, n); UP(ub_d, p->ub, n); UP(obj_d, h->obj.data(), n);
+    UP(vl_d, var_list.data(), var_list.size());
+    UP(ts_d, tiles_small.data(), tiles_small.size()); UP(tc_d, tiles_cta.data(), tiles_cta.size());
+    UP(th_d, tiles_hist.data(), tiles_hist.size()); UP(hc_d, hcols.data(), hcols.size());
+#undef UP
+    if (e == cudaSuccess && hist_bins > 0) e = cudaMemsetAsync(d.hbins, 0, sizeof(HBin) * hist_bins, st);
+    if (e == cudaSuccess && !hcols.empty()) e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
+    int cta_smem = max_cta_n * 20;
+    int hist_smem = max_hist_d * (int)sizeof(HBin);
+    if (e == cudaSuccess) e = setup_kernel_attributes(cta_smem, hist_smem);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "chap_bs_create: %s\n", cudaGetErrorString(e));
+        free_all(h);
+        delete h;
+        return CHAP_E_CUDA;
+    }
+    LaunchPlan &pl = h->plan;
+    pl.tiles_small = ts_d; pl.n_small = n_small;
+    pl.tiles_cta = tc_d; pl.n_cta = n_cta; pl.cta_smem = cta_smem;
+    pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = hist_smem;
+    int64_t apply_need = std::max<int64_t>(m, max_col);
+    pl.apply_blocks = (int)std::min<int64_t>(304, std::max<int64_t>(1, (apply_need + kApplyThreads - 1) / kApplyThreads));
+
+    chap_info &in = h->info;
+    in.n = n; in.m = m; in.m_norm = mn;
+    in.n_bin = n_bin; in.n_int = n_int; in.n_cont = n_cont; in.n_fixed = n_fixed;
+    in.nnz = p->nnz; in.nnz_int_rows = nnz_int; in.nnz_fp_rows = p->nnz - nnz_int;
+    in.eval_blocks = n_small + n_cta + (int)tiles_hist.size();
+    in.n_hist_cols = (int)hcols.size();
+    in.launches_per_step = (n_small > 0) + (n_cta > 0) + (!tiles_hist.empty()) + 2;
+    // algorithmic bytes of one pass: every nonzero once (row + coefficient),
+    // every row state and tolerance once, every active variable's state once.
+    int64_t n_act = n - n_fixed;
+    in.bytes_per_pass = 8 * nnz_int + 12 * (p->nnz - nnz_int) + 16LL * m + 8LL * m_fp +
+                        n_act * (8 /*x*/ + 8 /*column pointers*/ + 8 /*tabu*/ + 1 /*type*/) + nb_bytes_vars;
+
+    std::vector<double> x0(n);
+    for (int j = 0; j < n; ++j) x0[j] = std::min(std::max(0.0, h->lb[j]), h->ub[j]);
+    chap_status s = load_state(h, x0.data(), nullptr, nullptr, nullptr, 0, 0, 0);
+    if (s != CHAP_OK) {
+        std::fprintf(stderr, "chap_bs_create: %s\n", h->err.c_str());
+        free_all(h);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return CHAP_OK;
+}
+
+chap_status chap_bs_info(const chap_bs *h, chap_info *info)
+{
+    if (!h || !info) return CHAP_E_INVALID;
+    *info = h->info;
+    return CHAP_OK;
+}
+
+chap_status chap_bs_set_state(chap_bs *h, const double *x, const int32_t *w, int32_t mem)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    std::vector<double> xh;
+    std::vector<int> wh;
+    if (x) {
+        xh.resize(h->n);
+        if (mem == CHAP_MEM_HOST) std::copy(x, x + h->n, xh.begin());
+        else CK(h, cudaMemcpy(xh.data(), x, sizeof(double) * h->n, cudaMemcpyDeviceToHost), "read x");
+    } else {
+        xh.resize(h->n);
+        for (int j = 0; j < h->n; ++j) xh[j] = std::min(std::max(0.0, h->lb[j]), h->ub[j]);
+    }
+    if (w) {
+        wh.resize(h->m_norm);
+        if (mem == CHAP_MEM_HOST) std::copy(w, w + h->m_norm, wh.begin());
+        else CK(h, cudaMemcpy(wh.data(), w, sizeof(int) * h->m_norm, cudaMemcpyDeviceToHost), "read w");
+    }
+    return load_state(h, xh.data(), w ? wh.data() : nullptr, nullptr, nullptr, 0, 0, 0);
+}
+
+chap_status chap_bs_set_checkpoint(chap_bs *h, const double *x, const int32_t *w, const int64_t *tabu_inc,
+                                   const int64_t *tabu_dec, int64_t iter, int64_t best_nviol)
+{
+    if (!h || !x || !w || !tabu_inc || !tabu_dec) return h ? fail(h, CHAP_E_INVALID, "NULL checkpoint array") : CHAP_E_INVALID;
+    if (iter < 0 || iter > INT_MAX / 2) return fail(h, CHAP_E_INVALID, "iteration out of range");
+    std::vector<int> ti(h->n), td(h->n);
+    for (int j = 0; j < h->n; ++j) {
+        if (tabu_inc[j] < 0 || tabu_inc[j] > INT_MAX || tabu_dec[j] < 0 || tabu_dec[j] > INT_MAX)
+            return fail(h, CHAP_E_INVALID, "tabu stamp out of range");
+        ti[j] = (int)tabu_inc[j];
+        td[j] = (int)tabu_dec[j];
+    }
+    return load_state(h, x, w, ti.data(), td.data(), iter, best_nviol, 1);
+}
+
+chap_status chap_bs_get_state(chap_bs *h, double *x, int32_t *w, int64_t *tabu_inc, int64_t *tabu_dec,
+                              int64_t *scalars, int32_t mem)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    cudaMemcpyKind k = mem == CHAP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    Dev &d = h->dev;
+    if (x && h->n) CK(h, cudaMemcpyAsync(x, d.x, sizeof(double) * h->n, k, h->st), "copy x");
+    if (w && h->m) {
+        CK(h, launch_unpack_w(d, h->t_w, h->st), "unpack w");
+        CK(h, cudaMemcpyAsync(w, h->t_w, sizeof(int) * h->m_norm, k, h->st), "copy w");
+    }
+    if (tabu_inc && h->n) {
+        CK(h, launch_tabu_convert(h->n, d.tabu_inc, h->t_tabu, h->st), "widen tabu");
+        CK(h, cudaMemcpyAsync(tabu_inc, h->t_tabu, sizeof(long long) * h->n, k, h->st), "copy tabu");
+    }
+    if (tabu_dec && h->n) {
+        if (tabu_inc) CK(h, cudaStreamSynchronize(h->st), "synchronise");
+        CK(h, launch_tabu_convert(h->n, d.tabu_dec, h->t_tabu, h->st), "widen tabu");
+        CK(h, cudaMemcpyAsync(tabu_dec, h->t_tabu, sizeof(long long) * h->n, k, h->st), "copy tabu");
+    }
+    if (scalars || mem == CHAP_MEM_HOST) {
+        chap_status s = read_ctl(h);
+        if (s != CHAP_OK) return s;
+        if (scalars) {
+            scalars[0] = h->h_ctl->iter;
+            scalars[1] = h->h_ctl->nviol;
+            scalars[2] = h->h_ctl->best_nviol;
+            scalars[3] = h->h_ctl->feasible_iter;
+            scalars[4] = h->h_ctl->moves;
+            scalars[5] = h->h_ctl->bumps;
+        }
+    }
+    return CHAP_OK;
+}
+
+chap_status chap_bs_residuals(chap_bs *h, double *r, int32_t mem)
+{
+    if (!h || !r) return h ? fail(h, CHAP_E_INVALID, "NULL output") : CHAP_E_INVALID;
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    if (h->m == 0) return CHAP_OK;
+    CK(h, launch_unpack_r(h->dev, h->t_r, h->st), "unpack residuals");
+    CK(h, cudaMemcpyAsync(r, h->t_r, sizeof(double) * h->m_norm,
+                          mem == CHAP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st), "copy residuals");
+    if (mem == CHAP_MEM_HOST) CK(h, cudaStreamSynchronize(h->st), "synchronise");
+    return CHAP_OK;
+}
+
+chap_status chap_bs_best_shift(chap_bs *h, double *xhat, int64_t *score_half, int32_t *dnviol, chap_move *best,
+                               int32_t mem)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    VarOut o{nullptr, nullptr, nullptr};
+    bool host = mem == CHAP_MEM_HOST;
+    if (xhat) o.xhat = host ? h->t_xhat : xhat;
+    if (score_half) o.s = host ? h->t_s : reinterpret_cast<long long *>(score_half);
+    if (dnviol) o.dc = host ? h->t_dc : dnviol;
+    CK(h, launch_eval_gated(h->dev, h->plan, o, 0, h->st), "best-shift kernels");
+    CK(h, launch_select_gated(h->dev, 0, h->st), "selection kernel");
+    if (host && h->n) {
+        if (xhat) CK(h, cudaMemcpyAsync(xhat, h->t_xhat, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st), "copy xhat");
+        if (score_half) CK(h, cudaMemcpyAsync(score_half, h->t_s, sizeof(long long) * h->n, cudaMemcpyDeviceToHost, h->st), "copy scores");
+        if (dnviol) CK(h, cudaMemcpyAsync(dnviol, h->t_dc, sizeof(int) * h->n, cudaMemcpyDeviceToHost, h->st), "copy dnviol");
+    }
+    if (best || host) {
+        chap_status s = read_ctl(h);
+        if (s != CHAP_OK) return s;
+        if (best) {
+            const Ctl &c = *h->h_ctl;
+            best->var = c.mv_var;
+            best->dnviol = c.mv_dc;
+            best->score_half = c.mv_s;
+            best->old_value = c.mv_old;
+            best->new_value = c.mv_new;
+        }
+    }
+    return CHAP_OK;
+}
+
+chap_status chap_bs_apply(chap_bs *h, int32_t var, double new_value)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (var < -1 || var >= h->n) return fail(h, CHAP_E_INVALID, "variable index out of range");
+    if (var >= 0) {
+        if (!(new_value >= h->lb[var] && new_value <= h->ub[var])) return fail(h, CHAP_E_INVALID, "value outside the bounds");
+        if (h->vtype[var] != CHAP_VAR_CONT && !is_int_value(new_value)) return fail(h, CHAP_E_INVALID, "fractional value of an integer variable");
+        if (h->lb[var] == h->ub[var]) return fail(h, CHAP_E_INVALID, "fixed variable");
+    }
+    CK(h, launch_set_move(h->dev, var, new_value + 0.0, h->st), "set move");
+    CK(h, launch_apply_gated(h->dev, h->plan, 0, h->st), "apply kernel");
+    return CHAP_OK;
+}
+
+chap_status chap_bs_step(chap_bs *h, chap_move *out)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    VarOut o{nullptr, nullptr, nullptr};
+    CK(h, launch_eval_gated(h->dev, h->plan, o, 0, h->st), "best-shift kernels");
+    CK(h, launch_select_gated(h->dev, 0, h->st), "selection kernel");
+    CK(h, launch_apply_gated(h->dev, h->plan, 0, h->st), "apply kernel");
+    if (out) {
+        chap_status s = read_ctl(h);
+        if (s != CHAP_OK) return s;
+        const Ctl &c = *h->h_ctl;
+        out->var = c.mv_var;
+        out->dnviol = c.mv_dc;
+        out->score_half = c.mv_s;
+        out->old_value = c.mv_old;
+        out->new_value = c.mv_new;
+    }
+    return CHAP_OK;
+}
+
+chap_status chap_tabu_run(chap_bs *h, const chap_options *opts, chap_tabu_result *res)
+{
+    if (!h || !res) return h ? fail(h, CHAP_E_INVALID, "NULL result") : CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    chap_options o = opts ? *opts : h->opt;
+    if (o.graph_iters < 1 || o.max_iters < 0) return fail(h, CHAP_E_INVALID, "bad run options");
+    if (o.tenure != h->opt.tenure) return fail(h, CHAP_E_INVALID, "tenure is fixed at create time");
+    auto t0 = std::chrono::steady_clock::now();
+    chap_status s = read_ctl(h);
+    if (s != CHAP_OK) return s;
+    const long long iter0 = h->h_ctl->iter;
+    const long long moves0 = h->h_ctl->moves;
+    if (iter0 + o.max_iters + h->opt.tenure + 1 >= (long long)INT_MAX)
+        return fail(h, CHAP_E_UNSUPPORTED, "iteration counter would exceed the 32-bit tabu stamps");
+    Dev &d = h->dev;
+    CK(h, launch_begin_run(d, o.max_iters, o.stop_at_feasible, h->st), "begin run");
+    if (!h->gexec || h->g_iters != o.graph_iters) {
+        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+        cudaGraph_t g = nullptr;
+        CK(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal), "begin capture");
+        VarOut none{nullptr, nullptr, nullptr};
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < o.graph_iters && e == cudaSuccess; ++k) {
+            e = launch_eval_gated(d, h->plan, none, 1, h->cap_st);
+            if (e == cudaSuccess) e = launch_select_gated(d, 1, h->cap_st);
+            if (e == cudaSuccess) e = launch_apply_gated(d, h->plan, 1, h->cap_st);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capture"); }
+        if (e2 != cudaSuccess) return cuda_fail(h, e2, "end capture");
+        cudaError_t e3 = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e3, "instantiate graph"); }
+        h->g_iters = o.graph_iters;
+    }
+    long long max_replays = o.max_iters / o.graph_iters + 2;
+    for (long long r = 0; r < max_replays; ++r) {
+        CK(h, cudaGraphLaunch(h->gexec, h->st), "graph launch");
+        s = read_ctl(h);
+        if (s != CHAP_OK) return s;
+        if (h->h_ctl->done) break;
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    const Ctl c = *h->h_ctl;
+    res->iters = c.iter - iter0;
+    res->moves = c.moves - moves0;
+    res->feasible_iter = c.feasible_iter;
+    res->final_nviol = c.nviol;
+    res->best_nviol = c.best_nviol;
+    res->seconds = std::chrono::duration<double>(t1 - t0).count();
+    res->time_to_feasible_s = c.feasible_iter >= 0 ? (double)(c.t_feas_ns - c.t_start_ns) * 1e-9 : -1.0;
+    std::vector<double> x(h->n);
+    if (h->n) {
+        CK(h, cudaMemcpyAsync(x.data(), d.x, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st), "copy x");
+        CK(h, cudaStreamSynchronize(h->st), "synchronise");
+    }
+    double obj = 0.0;
+    for (int j = 0; j < h->n; ++j) obj += h->obj[j] * x[j];
+    res->objective = obj;
+    return CHAP_OK;
+}
+
+}  // extern "C"
