@@ -15,13 +15,6 @@
 #include <string>
 #include <vector>
 
-namespace chap {
-cudaError_t setup_kernel_attributes(int cta_smem, int hist_smem);
-cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
-cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st);
-cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
-}  // namespace chap
-
 using namespace chap;
 
 struct chap_bs {
@@ -166,6 +159,11 @@ void free_all(chap_bs *h)
     h->allocs.clear();
     if (h->h_ctl) { cudaFreeHost(h->h_ctl); h->h_ctl = nullptr; }
     if (h->cap_st) { cudaStreamDestroy(h->cap_st); h->cap_st = nullptr; }
+    for (int k = 0; k < 3; ++k) {
+        if (h->plan.side[k]) { cudaStreamDestroy(h->plan.side[k]); h->plan.side[k] = nullptr; }
+        if (h->plan.ev_join[k]) { cudaEventDestroy(h->plan.ev_join[k]); h->plan.ev_join[k] = nullptr; }
+    }
+    if (h->plan.ev_fork) { cudaEventDestroy(h->plan.ev_fork); h->plan.ev_fork = nullptr; }
 }
 
 chap_status read_ctl(chap_bs *h)
@@ -200,7 +198,7 @@ chap_status load_state(chap_bs *h, const double *x, const int *w, const int *tab
         int w1 = w ? w[k] : 1;
         int w2 = h->row_eq[i] ? (w ? w[k + 1] : 1) : -1;
         if (w1 < 1 || (h->row_eq[i] && w2 < 1)) return fail(h, CHAP_E_INVALID, "weights must be >= 1");
-        rs[i] = RowState{0, w1, w2};
+        rs[i] = RowState{0, w1, w2, 0.0, 0.0};
     }
     Dev &d = h->dev;
     CK(h, h2d(d.x, xc.data(), h->n, h->st), "copy x");
@@ -323,7 +321,74 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
     h->m_norm = mn;
 
-    // ---- split CSC (integral rows: int32 coefficients; others: double)
+    std::vector<double> row_val(p->nnz);
+    for (int i = 0; i < m; ++i)
+        for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e) row_val[e] = sign[i] * p->row_val[e];
+
+    // ---- classify variables
+    //  binary: streamed by T_BIN tiles; other columns by breakpoint entries (one
+    //  per normalised half plus the bounds): packed / warp bitonic in T_NB tiles
+    //  (<= kWarpSortMax), then multi-CTA counting sort (integer, domain <=
+    //  kHistMaxDomain) or CTA bitonic (<= kCtaMaxEntries).
+    std::vector<std::vector<int>> kind_vars(T_NUM_KINDS);
+    std::vector<int> fixed_vars;
+    std::vector<int> cta_n;  // padded entry count of each CTA-sorted column, in kind order
+    std::vector<int> nb_cap; // breakpoint entries of each T_NB column, in kind order
+    int n_bin = 0, n_int = 0, n_cont = 0;
+    int max_col = 0;
+    int64_t nb_bytes_vars = 0;
+    for (int j = 0; j < n; ++j) {
+        const int len = (int)(p->col_ptr[j + 1] - p->col_ptr[j]);
+        max_col = std::max(max_col, len);
+        if (h->lb[j] == h->ub[j]) { fixed_vars.push_back(j); continue; }
+        const int t = h->vtype[j];
+        if (t == CHAP_VAR_BIN) { ++n_bin; kind_vars[T_BIN].push_back(j); continue; }
+        (t == CHAP_VAR_INT ? n_int : n_cont)++;
+        nb_bytes_vars += 16;
+        const bool fin = std::isfinite(h->lb[j]) && std::isfinite(h->ub[j]);
+        const double dom = fin ? h->ub[j] - h->lb[j] + 1 : INFINITY;
+        int64_t E = (std::isfinite(h->lb[j]) ? 1 : 0) + (std::isfinite(h->ub[j]) ? 1 : 0);
+        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += h->row_eq[p->row_idx[e]] ? 2 : 1;
+        int k;
+        if (E <= kWarpSortMax) k = T_NB;
+        else if (t == CHAP_VAR_INT && dom <= kHistMaxDomain) k = T_NB_HIST;
+        else if (E <= kCtaMaxEntries) k = T_NB_CTA;
+        else {
+            std::fprintf(stderr, "chap_bs_create: column %d has %lld breakpoint entries and no on-chip path\n", j, (long long)E);
+            delete h;
+            return CHAP_E_UNSUPPORTED;
+        }
+        if (k == T_NB_CTA) cta_n.push_back(std::max(next_pow2((int)E), kCtaThreads));
+        if (k == T_NB) nb_cap.push_back((int)E);
+        kind_vars[k].push_back(j);
+    }
+    {
+        // short columns are evaluated one per thread: order them by entry count so
+        // that the threads of a warp do similar work
+        std::vector<int> ord(nb_cap.size());
+        for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return nb_cap[x] < nb_cap[y]; });
+        std::vector<int> vs(ord.size()), cs(ord.size());
+        for (size_t q = 0; q < ord.size(); ++q) { vs[q] = kind_vars[T_NB][ord[q]]; cs[q] = nb_cap[ord[q]]; }
+        kind_vars[T_NB].swap(vs);
+        nb_cap.swap(cs);
+    }
+    const int n_fixed = (int)fixed_vars.size();
+    std::vector<int> var_list;
+    var_list.reserve(n);
+    std::vector<int> kind_base(T_NUM_KINDS + 1, 0);
+    for (int k = 0; k < T_NUM_KINDS; ++k) {
+        kind_base[k] = (int)var_list.size();
+        var_list.insert(var_list.end(), kind_vars[k].begin(), kind_vars[k].end());
+    }
+    kind_base[T_NUM_KINDS] = (int)var_list.size();
+    var_list.insert(var_list.end(), fixed_vars.begin(), fixed_vars.end());
+    std::vector<long long> nb_off(nb_cap.size() + 1, 0);  // list offsets of the T_NB columns
+    for (size_t k = 0; k < nb_cap.size(); ++k) nb_off[k + 1] = nb_off[k] + nb_cap[k];
+    std::vector<int> vpos(n);
+    for (int q = 0; q < n; ++q) vpos[var_list[q]] = q;
+
+    // ---- split CSC in var_list order (integral rows: int32 coefficients; others: double)
     std::vector<int> ci_ptr(n + 1, 0), cf_ptr(n + 1, 0);
     std::vector<int> ci_row, ci_val, cf_row;
     std::vector<double> cf_val;
@@ -331,113 +396,80 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     ci_val.reserve(nnz_int);
     cf_row.reserve(p->nnz - nnz_int);
     cf_val.reserve(p->nnz - nnz_int);
-    for (int j = 0; j < n; ++j) {
+    for (int q = 0; q < n; ++q) {
+        const int j = var_list[q];
         for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) {
-            int i = p->row_idx[e];
-            double a = sign[i] * p->col_val[e];
+            const int i = p->row_idx[e];
+            const double a = sign[i] * p->col_val[e];
             if (rint[i]) { ci_row.push_back(i); ci_val.push_back((int)a); }
             else { cf_row.push_back(i); cf_val.push_back(a); }
         }
-        ci_ptr[j + 1] = (int)ci_row.size();
-        cf_ptr[j + 1] = (int)cf_row.size();
+        ci_ptr[q + 1] = (int)ci_row.size();
+        cf_ptr[q + 1] = (int)cf_row.size();
     }
-    std::vector<double> row_val(p->nnz);
-    for (int i = 0; i < m; ++i)
-        for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e) row_val[e] = sign[i] * p->row_val[e];
 
-    // ---- classify variables and build work tiles
-    std::vector<std::vector<int>> kind_vars(T_NB_HIST + 1);
-    int n_bin = 0, n_int = 0, n_cont = 0, n_fixed = 0;
-    int max_col = 0;
-    int64_t nb_bytes_vars = 0;
-    for (int j = 0; j < n; ++j) {
-        int nI = ci_ptr[j + 1] - ci_ptr[j], nF = cf_ptr[j + 1] - cf_ptr[j];
-        int len = nI + nF;
-        max_col = std::max(max_col, len);
-        if (h->lb[j] == h->ub[j]) { ++n_fixed; continue; }
-        int t = h->vtype[j];
-        if (t == CHAP_VAR_BIN) {
-            ++n_bin;
-            int k = len <= 4 ? T_BIN_G4 : len <= 8 ? T_BIN_G8 : len <= 16 ? T_BIN_G16 : len <= 2048 ? T_BIN_G32 : T_BIN_CTA;
-            kind_vars[k].push_back(j);
-            continue;
-        }
-        (t == CHAP_VAR_INT ? n_int : n_cont)++;
-        nb_bytes_vars += 16;
-        int64_t E = (std::isfinite(h->lb[j]) ? 1 : 0) + (std::isfinite(h->ub[j]) ? 1 : 0);
-        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += h->row_eq[p->row_idx[e]] ? 4 : 2;
-        int k;
-        if (E <= 32) k = T_NB_K1;
-        else if (E <= 64) k = T_NB_K2;
-        else if (E <= 128) k = T_NB_K4;
-        else if (E <= 256) k = T_NB_K8;
-        else if (E <= kCtaMaxEntries) k = T_NB_CTA;
-        else if (t == CHAP_VAR_INT && std::isfinite(h->lb[j]) && std::isfinite(h->ub[j]) &&
-                 h->ub[j] - h->lb[j] + 1 <= kHistMaxDomain) k = T_NB_HIST;
-        else {
-            std::fprintf(stderr, "chap_bs_create: column %d has %lld breakpoint entries and no on-chip path\n", j, (long long)E);
-            delete h;
-            return CHAP_E_UNSUPPORTED;
-        }
-        kind_vars[k].push_back(j);
-    }
-    std::vector<int> var_list;
-    std::vector<Tile> tiles_small, tiles_cta, tiles_hist;
+    // ---- work tiles
+    std::vector<Tile> tiles_bin, tiles_nb, tiles_cta, tiles_hist;
     std::vector<HistCol> hcols;
     int max_cta_n = 0, max_hist_d = 0;
     int64_t hist_bins = 0;
-    for (int k = 0; k <= T_NB_HIST; ++k) {
-        const std::vector<int> &vs = kind_vars[k];
-        int base = (int)var_list.size();
-        var_list.insert(var_list.end(), vs.begin(), vs.end());
-        int cnt = (int)vs.size();
+    {
+        // binary: consecutive columns up to ~kBinTileEntries nonzeros and kBinMaxCols columns
+        const int q0 = kind_base[T_BIN], q1 = kind_base[T_BIN + 1];
+        int start = q0;
+        int64_t ent = 0;
+        for (int q = q0; q < q1; ++q) {
+            const int64_t len = (int64_t)(ci_ptr[q + 1] - ci_ptr[q]) + (cf_ptr[q + 1] - cf_ptr[q]);
+            if (q > start && (ent + len > kBinTileEntries || q - start >= kBinMaxCols)) {
+                tiles_bin.push_back(Tile{T_BIN, start, q, 0});
+                start = q;
+                ent = 0;
+            }
+            ent += len;
+        }
+        if (q1 > start) tiles_bin.push_back(Tile{T_BIN, start, q1, 0});
+    }
+    for (int k = T_NB; k < T_NUM_KINDS; ++k) {
+        const int base = kind_base[k], cnt = kind_base[k + 1] - base;
         if (cnt == 0) continue;
-        if (k <= T_BIN_G32) {
-            int G = 4 << (k - T_BIN_G4);
-            int per = (kEvalThreads / G) * 4;
-            for (int b = 0; b < cnt; b += per) tiles_small.push_back(Tile{k, base + b, base + std::min(cnt, b + per), 0});
-        } else if (k == T_BIN_CTA) {
-            for (int b = 0; b < cnt; ++b) tiles_small.push_back(Tile{k, base + b, base + b + 1, 0});
-        } else if (k <= T_NB_K8) {
-            int per = (kEvalThreads / 32) * 2;
-            for (int b = 0; b < cnt; b += per) tiles_small.push_back(Tile{k, base + b, base + std::min(cnt, b + per), 0});
+        if (k == T_NB) {
+            for (int b = 0; b < cnt; b += kNbThreads) tiles_nb.push_back(Tile{k, base + b, base + std::min(cnt, b + kNbThreads), 0});
         } else if (k == T_NB_CTA) {
             for (int b = 0; b < cnt; ++b) {
-                int j = vs[b];
-                int64_t E = (std::isfinite(h->lb[j]) ? 1 : 0) + (std::isfinite(h->ub[j]) ? 1 : 0);
-                for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += h->row_eq[p->row_idx[e]] ? 4 : 2;
-                int N = std::max(next_pow2((int)E), kCtaThreads);
-                max_cta_n = std::max(max_cta_n, N);
-                tiles_cta.push_back(Tile{k, base + b, base + b + 1, N});
+                max_cta_n = std::max(max_cta_n, cta_n[b]);
+                tiles_cta.push_back(Tile{k, base + b, base + b + 1, cta_n[b]});
             }
         } else {
             for (int b = 0; b < cnt; ++b) {
-                int j = vs[b];
+                const int q = base + b, j = var_list[q];
                 HistCol hc{};
-                hc.var = j;
-                int D = (int)(h->ub[j] - h->lb[j]) + 1;
+                hc.pos = q;
+                const int D = (int)(h->ub[j] - h->lb[j]) + 1;
                 max_hist_d = std::max(max_hist_d, D);
                 hc.bin_off = hist_bins;
                 hist_bins += D;
-                hc.e_begin = 0;
-                hc.e_mid = ci_ptr[j + 1] - ci_ptr[j];
-                hc.e_end = hc.e_mid + (cf_ptr[j + 1] - cf_ptr[j]);
+                hc.e_mid = ci_ptr[q + 1] - ci_ptr[q];
+                hc.e_end = hc.e_mid + (cf_ptr[q + 1] - cf_ptr[q]);
                 hc.nchunks = std::max(1, (hc.e_end + kHistChunk - 1) / kHistChunk);
-                int hidx = (int)hcols.size();
+                const int hidx = (int)hcols.size();
                 for (int c = 0; c < hc.nchunks; ++c) tiles_hist.push_back(Tile{k, hidx, hidx + 1, c});
                 hcols.push_back(hc);
             }
         }
     }
-    const int n_small = (int)tiles_small.size(), n_cta = (int)tiles_cta.size();
-    for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = n_small + n_cta + (int)q;
-    const int n_bb = n_small + n_cta + (int)hcols.size();
+    const int n_tb = (int)tiles_bin.size(), n_tn = (int)tiles_nb.size(), n_tc = (int)tiles_cta.size();
+    const int slot_hist = n_tb + n_tn + n_tc;
+    for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = slot_hist + (int)q;
+    const int n_bb = slot_hist + (int)hcols.size();
 
     // ---- device allocation
     Dev &d = h->dev;
     d.n = n;
     d.m = m;
     d.tenure = h->opt.tenure;
+    // the nonzero arrays are padded by 8 elements: kernels read aligned groups of 8
+    ci_row.resize(ci_row.size() + 8, 0); ci_val.resize(ci_val.size() + 8, 0);
+    cf_row.resize(cf_row.size() + 8, 0); cf_val.resize(cf_val.size() + 8, 0.0);
     int *ci_ptr_d = dalloc<int>(h, n + 1), *ci_row_d = dalloc<int>(h, ci_row.size()), *ci_val_d = dalloc<int>(h, ci_val.size());
     int *cf_ptr_d = dalloc<int>(h, n + 1), *cf_row_d = dalloc<int>(h, cf_row.size());
     double *cf_val_d = dalloc<double>(h, cf_val.size());
@@ -454,12 +486,19 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     d.tabu_dec = dalloc<int>(h, n);
     d.ctl = dalloc<Ctl>(h, 1);
     int *vl_d = dalloc<int>(h, var_list.size());
+    int *vpos_d = dalloc<int>(h, n);
     d.block_best = dalloc<Cand>(h, n_bb);
     d.n_block_best = n_bb;
-    Tile *ts_d = dalloc<Tile>(h, tiles_small.size()), *tc_d = dalloc<Tile>(h, tiles_cta.size()), *th_d = dalloc<Tile>(h, tiles_hist.size());
+    Tile *tb_d = dalloc<Tile>(h, tiles_bin.size()), *tn_d = dalloc<Tile>(h, tiles_nb.size());
+    Tile *tc_d = dalloc<Tile>(h, tiles_cta.size());
+    Tile *th_d = dalloc<Tile>(h, tiles_hist.size());
     HistCol *hc_d = dalloc<HistCol>(h, hcols.size());
     d.hbins = dalloc<HBin>(h, hist_bins);
     d.hacc = dalloc<HistAcc>(h, hcols.size());
+    d.lists = dalloc<SEntry>(h, (size_t)nb_off.back());
+    long long *nb_off_d = dalloc<long long>(h, nb_off.size());
+    d.list_off = nb_off_d;
+    d.nb_pos0 = kind_base[T_NB];
     h->t_xhat = dalloc<double>(h, n);
     h->t_s = dalloc<long long>(h, n);
     h->t_dc = dalloc<int>(h, n);
@@ -468,10 +507,14 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     h->t_tabu = dalloc<long long>(h, n);
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && row_ptr_d && col_idx_d &&
               row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.rs &&
-              d.tabu_inc && d.tabu_dec && d.ctl && vl_d && d.block_best && ts_d && tc_d && th_d && hc_d &&
-              d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
+              d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tb_d && tn_d && tc_d && th_d && hc_d &&
+              d.hbins && d.hacc && d.lists && nb_off_d && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
     if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
+    for (int k = 0; k < 3 && ok; ++k)
+        if (cudaStreamCreateWithFlags(&h->plan.side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->plan.ev_join[k], cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); ok = false; }
+    if (ok && cudaEventCreateWithFlags(&h->plan.ev_fork, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); ok = false; }
     if (!ok) {
         free_all(h);
         delete h;
@@ -483,6 +526,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     d.rhs = rhs_d; d.eps = eps_d; d.row_int = rint_d; d.nrow_base = nrb_d;
     d.vtype = vt_d; d.lb = lb_d; d.ub = ub_d; d.obj = obj_d;
     d.var_list = vl_d;
+    d.vpos = vpos_d;
     d.hcols = hc_d;
     cudaStream_t st = h->st;
     std::vector<long long> rp(p->row_ptr, p->row_ptr + m + 1);
@@ -493,16 +537,22 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     UP(row_ptr_d, rp.data(), m + 1); UP(col_idx_d, p->col_idx, p->nnz); UP(row_val_d, row_val.data(), p->nnz);
     UP(rhs_d, rhs.data(), m); UP(eps_d, eps.data(), m); UP(rint_d, rint.data(), m); UP(nrb_d, h->nrow_base.data(), m);
     UP(vt_d, p->vtype, n); UP(lb_d, p->lb, n); UP(ub_d, p->ub, n); UP(obj_d, h->obj.data(), n);
-    UP(vl_d, var_list.data(), var_list.size());
-    UP(ts_d, tiles_small.data(), tiles_small.size()); UP(tc_d, tiles_cta.data(), tiles_cta.size());
+    UP(vl_d, var_list.data(), var_list.size()); UP(vpos_d, vpos.data(), n);
+    UP(tb_d, tiles_bin.data(), tiles_bin.size()); UP(tn_d, tiles_nb.data(), tiles_nb.size());
+    UP(tc_d, tiles_cta.data(), tiles_cta.size());
     UP(th_d, tiles_hist.data(), tiles_hist.size()); UP(hc_d, hcols.data(), hcols.size());
+    UP(nb_off_d, nb_off.data(), nb_off.size());
 #undef UP
     if (e == cudaSuccess && hist_bins > 0) e = cudaMemsetAsync(d.hbins, 0, sizeof(HBin) * hist_bins, st);
     if (e == cudaSuccess && !hcols.empty()) e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
-    int cta_smem = max_cta_n * 20;
-    int hist_smem = max_hist_d * (int)sizeof(HBin);
-    if (e == cudaSuccess) e = setup_kernel_attributes(cta_smem, hist_smem);
+    LaunchPlan &pl = h->plan;
+    pl.tiles_bin = tb_d; pl.n_bin = n_tb;
+    pl.tiles_nb = tn_d; pl.n_nb = n_tn; pl.nb_smem = 0;
+    pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
+    pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);
+    pl.slot_nb = n_tb; pl.slot_cta = n_tb + n_tn;
+    if (e == cudaSuccess) e = setup_kernel_attributes(pl);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         std::fprintf(stderr, "chap_bs_create: %s\n", cudaGetErrorString(e));
@@ -510,10 +560,6 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         delete h;
         return CHAP_E_CUDA;
     }
-    LaunchPlan &pl = h->plan;
-    pl.tiles_small = ts_d; pl.n_small = n_small;
-    pl.tiles_cta = tc_d; pl.n_cta = n_cta; pl.cta_smem = cta_smem;
-    pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = hist_smem;
     int64_t apply_need = std::max<int64_t>(m, max_col);
     pl.apply_blocks = (int)std::min<int64_t>(304, std::max<int64_t>(1, (apply_need + kApplyThreads - 1) / kApplyThreads));
 
@@ -521,13 +567,13 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     in.n = n; in.m = m; in.m_norm = mn;
     in.n_bin = n_bin; in.n_int = n_int; in.n_cont = n_cont; in.n_fixed = n_fixed;
     in.nnz = p->nnz; in.nnz_int_rows = nnz_int; in.nnz_fp_rows = p->nnz - nnz_int;
-    in.eval_blocks = n_small + n_cta + (int)tiles_hist.size();
+    in.eval_blocks = n_tb + n_tn + n_tc + (int)tiles_hist.size();
     in.n_hist_cols = (int)hcols.size();
-    in.launches_per_step = (n_small > 0) + (n_cta > 0) + (!tiles_hist.empty()) + 2;
+    in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + 2;
     // algorithmic bytes of one pass: every nonzero once (row + coefficient),
     // every row state and tolerance once, every active variable's state once.
     int64_t n_act = n - n_fixed;
-    in.bytes_per_pass = 8 * nnz_int + 12 * (p->nnz - nnz_int) + 16LL * m + 8LL * m_fp +
+    in.bytes_per_pass = 8 * nnz_int + 12 * (p->nnz - nnz_int) + 16LL * (m - m_fp) + 32LL * m_fp +
                         n_act * (8 /*x*/ + 8 /*column pointers*/ + 8 /*tabu*/ + 1 /*type*/) + nb_bytes_vars;
 
     std::vector<double> x0(n);

@@ -6,15 +6,21 @@
 //    evaluated as its two normalised halves (a, b) and (-a, -b) (Sec. 3.1,
 //    "Memory Considerations", second point), which avoids storing its nonzeros
 //    twice.
-//  - RowState (16 B, one coalesced load per nonzero gather): the residual
+//  - RowState (32 B = one sector per nonzero gather): the residual
 //    r = a.x - b of the first half (int64 on integral rows, IEEE double bits on
-//    the others) and the integer weights of both halves (w2 = -1 for a single
-//    row).  Storing r instead of the activity is the paper's first memory point.
+//    the others), the integer weights of both halves (w2 = -1 for a single row)
+//    and, on non-integral rows, the margins eps - r and eps + r, so that every
+//    violation test of the flip and breakpoint code is a sign or ordered-key
+//    comparison (no FP64 arithmetic per nonzero; GB300's FP64 rate is low).
+//    Storing r instead of the activity is the paper's first memory point.
 //  - Two CSC matrices: CSC_I holds the nonzeros of integral rows (int32 row,
 //    int32 coefficient: 8 B/nnz), CSC_F those of the other rows (int32 row,
-//    double coefficient: 12 B/nnz).  A column j owns ci_ptr[j]..ci_ptr[j+1] and
-//    cf_ptr[j]..cf_ptr[j+1]; the arithmetic type of a nonzero is known from the
-//    matrix it sits in, so no per-row flag is gathered.
+//    double coefficient: 12 B/nnz).  Columns are stored in evaluation order
+//    var_list (binary columns first, then each non-binary class), so the
+//    binary pass streams one contiguous range; position q (var_list[q] = j,
+//    vpos[j] = q) owns ci_ptr[q]..ci_ptr[q+1] and cf_ptr[q]..cf_ptr[q+1].  The
+//    arithmetic type of a nonzero is known from the matrix it sits in, so no
+//    per-row flag is gathered.
 //  - CSR (double) of the physical rows, used only to recompute residuals from
 //    scratch when a state is set.
 #pragma once
@@ -25,10 +31,12 @@ namespace chap {
 
 constexpr int kVarBin = 0, kVarInt = 1, kVarCont = 2;
 
-struct __align__(16) RowState {
+struct __align__(32) RowState {
     long long r;  // int64 residual or the bits of a double residual
     int w1;       // weight of the first normalised half
     int w2;       // weight of the second half of an "=" row, -1 otherwise
+    double m1;    // non-integral rows: eps - r  (first half violated  <=> m1 < 0)
+    double m2;    // non-integral rows: eps + r  (second half violated <=> m2 < 0)
 };
 
 // Best move of a CTA (or of the whole pass): larger s wins, then lower var.
@@ -67,35 +75,38 @@ struct __align__(16) Ctl {
 
 // Work tiles of the best-shift pass.  A tile covers var_list[begin, end).
 enum TileKind : int {
-    T_BIN_G4 = 0, T_BIN_G8, T_BIN_G16, T_BIN_G32, T_BIN_CTA,   // binary flips, G lanes per column
-    T_NB_K1, T_NB_K2, T_NB_K4, T_NB_K8,                         // warp sort of <= 32K entries
-    T_NB_CTA,                                                   // CTA sort in shared memory
-    T_NB_HIST                                                   // multi-CTA key histogram (integer keys)
+    T_BIN = 0,                // binary flips: consecutive columns streamed by one CTA
+    T_NB,                     // short breakpoint lists: packed / warp bitonic sorts
+    T_NB_CTA,                 // CTA bitonic sort in shared memory
+    T_NB_HIST,                // multi-CTA counting sort (long integer columns)
+    T_NUM_KINDS
 };
 
 struct Tile {
     int kind;
-    int begin;
-    int end;
-    int aux;   // T_NB_CTA: padded entry count; T_NB_HIST: chunk index
+    int begin;   // first position (var_list index) of the tile
+    int end;     // one past the last position
+    int aux;     // T_NB_CTA: padded entry count; T_NB_HIST: chunk index
 };
 
-// Histogram bin of one integer value v of a long integer column (T_NB_HIST).
-struct __align__(16) HBin {
-    long long sm;  // sum of the score deltas of the entries (v, -1)
-    long long sp;  // sum of the score deltas of the entries (v, +1)
-    int cm;        // sum of the count deltas of the entries (v, -1)
-    int cp;        // sum of the count deltas of the entries (v, +1)
-    int np;        // number of entries (v, -1): v is a candidate when > 0
-    int pad;
+// Counting-sort bin of one integer value v of a column: the entries (v, pre)
+// carry score deltas that count at v, the entries (v, post) deltas that count
+// right of v; every pre entry lowers the violation count by one, every post
+// entry raises it by one (Algorithm 1 case table).
+struct __align__(8) HBin {
+    long long spre;
+    long long spost;
+    int n1;   // number of pre entries at v
+    int n2;   // number of post entries at v
 };
 
 struct HistCol {
-    int var;
+    int pos;              // position of the column in var_list
     int nchunks;
     long long bin_off;    // offset of the column's bins in the HBin scratch
-    int e_begin, e_mid, e_end;  // virtual entry range: [0, e_mid) integral part, [e_mid, e_end) FP part
+    int e_mid, e_end;     // virtual entry range: [0, e_mid) integral part, [e_mid, e_end) FP part
     int slot;             // block_best slot of the column
+    int pad;
 };
 
 // Accumulators of one histogram column (global, reset after use).
@@ -110,7 +121,7 @@ struct Dev {
     int n, m;
     int tenure;
     int pad0;
-    // CSC split
+    // CSC split, columns in var_list order (pointers indexed by position)
     const int *ci_ptr, *ci_row, *ci_val;
     const int *cf_ptr, *cf_row;
     const double *cf_val;
@@ -131,13 +142,28 @@ struct Dev {
     int *tabu_inc, *tabu_dec;
     Ctl *ctl;
     // best-shift work
-    const int *var_list;
+    const int *var_list;     // position -> variable
+    const int *vpos;         // variable -> position
     Cand *block_best;
     int n_block_best;
     int pad1;
     HBin *hbins;
     HistAcc *hacc;
     const HistCol *hcols;
+    // scratch of the short non-binary columns: the breakpoint entries inside
+    // [l, u] of position q are written to lists[list_off[q - nb_pos0] ...]
+    struct SEntry *lists;
+    const long long *list_off;
+    int nb_pos0;
+    int pad2;
+};
+
+// Breakpoint entry of a short non-binary column: key (t in order-preserving
+// form), score delta (|delta| <= 2w < 2^31), aux = post marker and count delta.
+struct __align__(16) SEntry {
+    unsigned long long key;
+    int del;
+    unsigned aux;
 };
 
 // Optional per-variable outputs of a best-shift pass (device pointers, may be null).
@@ -147,40 +173,54 @@ struct VarOut {
     int *dc;
 };
 
-// Kernel launchers (kernels.cu).  All are asynchronous on `st`.
 struct LaunchPlan {
-    const Tile *tiles_small;   // device
-    int n_small;
-    const Tile *tiles_cta;     // device
+    const Tile *tiles_bin;     // device
+    int n_bin;
+    const Tile *tiles_nb;      // non-binary tiles (breakpoint lists of <= kWarpSortMax entries)
+    int n_nb;
+    int nb_smem;
+    const Tile *tiles_cta;
     int n_cta;
     int cta_smem;              // dynamic shared memory of the CTA-sort kernel
-    const Tile *tiles_hist;    // device
+    const Tile *tiles_hist;
     int n_hist_tiles;
     int hist_smem;
+    int slot_nb, slot_cta;     // first block_best slot of each kernel
     int apply_blocks;
+    cudaStream_t side[3];      // side streams of the non-binary evaluation kernels
+    cudaEvent_t ev_fork, ev_join[3];
 };
 
-cudaError_t launch_eval(const Dev &d, const LaunchPlan &p, const VarOut &o, cudaStream_t st);
-cudaError_t launch_select(const Dev &d, cudaStream_t st);
-cudaError_t launch_apply(const Dev &d, const LaunchPlan &p, cudaStream_t st);
+// Kernel launchers (kernels.cu).  All are asynchronous on `st`; `gate` makes a
+// kernel return at once when the run's done flag is set (graph replays).
+cudaError_t setup_kernel_attributes(const LaunchPlan &p);
+cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
+cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st);
+cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
 cudaError_t launch_set_move(const Dev &d, int var, double new_value, cudaStream_t st);
 cudaError_t launch_residuals(const Dev &d, cudaStream_t st);
 cudaError_t launch_finish_set_state(const Dev &d, long long iter, long long best_nviol, int use_best, cudaStream_t st);
 cudaError_t launch_begin_run(const Dev &d, long long max_iters, int stop_at_feasible, cudaStream_t st);
-cudaError_t launch_pack_w(const Dev &d, const int *w_norm, cudaStream_t st);
 cudaError_t launch_unpack_w(const Dev &d, int *w_norm, cudaStream_t st);
 cudaError_t launch_unpack_r(const Dev &d, double *r_norm, cudaStream_t st);
 cudaError_t launch_tabu_convert(int n, const int *src32, long long *dst64, cudaStream_t st);
-cudaError_t launch_tabu_narrow(int n, const long long *src64, int *dst32, cudaStream_t st);
 
 // Sizes used by both sides.
 constexpr int kEvalThreads = 256;
-constexpr int kWarpStageCap = 256;     // entries staged per warp (K <= 8)
-constexpr int kCtaMaxEntries = 8192;   // largest column list sorted by one CTA
+constexpr int kWarpStageCap = 128;      // entries staged per warp (K <= 4)
+constexpr int kCtaMaxEntries = 8192;    // largest entry list sorted by one CTA
 constexpr int kCtaThreads = 512;
-constexpr int kHistMaxDomain = 4096;   // largest integer domain of the histogram path
-constexpr int kHistChunk = 16384;      // matrix entries per histogram CTA
+constexpr int kHistMaxDomain = 4096;    // largest integer domain of the multi-CTA counting sort
+constexpr int kHistChunk = 16384;       // matrix entries per counting-sort CTA
 constexpr int kHistThreads = 512;
 constexpr int kApplyThreads = 256;
+constexpr int kBinChunk = 2048;         // nonzeros staged in shared memory per binary sub-chunk
+constexpr int kBinTileEntries = 4096;   // target nonzeros of one binary tile
+constexpr int kBinMaxCols = 1024;       // columns of one binary tile
+constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
+constexpr int kNbThreads = 128;         // short non-binary columns per CTA (one thread each)
+constexpr int kTileMaxCols = 64;        // columns of one non-binary tile
+constexpr int kTileSlots = 4096;        // sort-entry slots (16 B) of one non-binary tile
+constexpr int kTileEntries = 2048;      // nonzeros of one non-binary tile (its exact-pass queue holds 2 per nonzero)
 
 }  // namespace chap

@@ -1,31 +1,35 @@
 // Kernels of the best-shift tabu search (sm_103a).
 //
-// One tabu iteration = best-shift pass (eval kernels) -> selection -> apply.
+// One tabu iteration = best-shift pass (evaluation kernels) -> selection -> apply.
 //
-//  * Binary columns: the only move is the flip (Sec. 3.1, "Best Shift Moves");
-//    its score is a segmented sum of penalties over the column.  G lanes work
-//    on one column (G = 4..32 by column length, or a whole CTA for very long
-//    columns); nonzeros are read coalesced inside the column and the row
-//    residual + weights are gathered with one 16-byte load.
-//  * Other columns: Algorithm 1 (sort -> scan -> argmax).  Breakpoint entries
-//    (t, marker, score delta, count delta) are generated from each nonzero,
-//    entries below l are folded into the base beta, entries above u are
-//    dropped, and the rest are
-//      - sorted by a warp-level bitonic network held in registers (up to 32K
-//        entries, K per lane), or
-//      - sorted in shared memory by one CTA (up to kCtaMaxEntries), or
-//      - bucketed by key (an integer counting sort) across many CTAs for long
-//        integer columns with small domains;
-//    then prefix-scanned, and reduced to the best admissible entry.
-//  * Each CTA reduces its columns to one candidate; the selection kernel
-//    reduces the CTA candidates (largest score, then lowest variable).
-//  * Apply walks the chosen column and updates the residuals incrementally
+//  * Binary columns (k_eval_bin): the only move is the flip (Sec. 3.1, "Best
+//    Shift Moves"); its score is a segmented sum of penalties over the column.
+//    G lanes work on one column (G = 4..32 by column length, a whole CTA for very
+//    long columns); each lane keeps four nonzeros in flight, reads them
+//    coalesced inside the column and gathers the row state with one sector.
+//  * Other columns: Algorithm 1 (sort -> scan -> argmax).  Breakpoint entries are
+//    generated from each nonzero (`half_case`, the case table of Algorithm 1);
+//    an a<0 half gives one "pre" entry (its delta counts at t), an a>0 half one
+//    "post" entry (t is a candidate and its delta counts right of t: the two
+//    entries of Algorithm 1 merged).  Entries below l fold into beta, entries
+//    above u are dropped.  The entries of one column are then
+//      - counting-sorted by integer value in shared memory by one warp
+//        (k_eval_hw: integer variables with a domain of at most 256 values), or
+//      - bitonic-sorted in registers by one warp, K entries per lane
+//        (k_eval_sort: up to 256 entries), or
+//      - bitonic-sorted in shared memory by one CTA (k_eval_cta: up to 8192), or
+//      - counting-sorted across many CTAs (k_eval_hist: long integer columns),
+//    prefix-scanned, and reduced to the best admissible candidate.
+//  * Every CTA reduces its columns to one candidate; k_select reduces the CTA
+//    candidates (largest score, then lowest variable).
+//  * k_apply walks the chosen column and updates the residuals incrementally
 //    (Sec. 3.1, "Memory Considerations", first point); when no positive move
 //    exists it adds 1 to the weight of every violated normalised row.
 //
-// All arithmetic that decides a score is exact: integral rows use int64
-// residuals, non-integral rows IEEE double with explicit round-to-nearest
-// intrinsics (no fused multiply-add), and scores are int64 half-weight counts.
+// Exactness: integral rows use int64 residuals and integer arithmetic only;
+// non-integral rows keep r, eps - r and eps + r (double, explicit
+// round-to-nearest, no contraction), and every comparison of doubles is done on
+// order-preserving integer keys.  Scores are int64 half-weight counts.
 #include "chap_internal.h"
 
 #include <climits>
@@ -35,46 +39,74 @@ namespace chap {
 
 #define FULLMASK 0xffffffffu
 
-constexpr unsigned long long kPadKey = 0xffffffffffffffffull;
+constexpr unsigned long long kSign = 0x8000000000000000ull;
+constexpr unsigned long long kPadKey = ~0ull;
 constexpr int kNoVar = INT_MAX;
+constexpr long long kDdMax = 1LL << 60;
 
 // ---------------------------------------------------------------- helpers
 
-// Order-preserving map of a double to an unsigned 64-bit key.
-__device__ __forceinline__ unsigned long long ord_key(double t)
+// Order-preserving maps of doubles and int64 to unsigned 64-bit keys.
+__device__ __forceinline__ unsigned long long dkey(double t)
 {
     unsigned long long b = (unsigned long long)__double_as_longlong(t);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    return (b & kSign) ? ~b : (b | kSign);
 }
 
-__device__ __forceinline__ double key_to_double(unsigned long long k)
+__device__ __forceinline__ double dkey_val(unsigned long long k)
 {
-    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    unsigned long long b = (k & kSign) ? (k & ~kSign) : ~k;
     return __longlong_as_double((long long)b);
 }
 
-__device__ __forceinline__ long long floor_div(long long a, long long b)
+__device__ __forceinline__ unsigned long long ikey(long long t) { return (unsigned long long)t ^ kSign; }
+__device__ __forceinline__ long long ikey_val(unsigned long long k) { return (long long)(k ^ kSign); }
+
+// Sign of a double that is never -0.0 here (margins are eps -+ r rounded to nearest).
+__device__ __forceinline__ bool dneg(double v) { return __double_as_longlong(v) < 0; }
+__device__ __forceinline__ bool dgt(double a, double b) { return dkey(a) > dkey(b); }
+// -v by flipping the sign bit (keeps the FP64 pipe free).
+__device__ __forceinline__ double dflip(double v) { return __longlong_as_double(__double_as_longlong(v) ^ (long long)kSign); }
+
+// Single-precision estimate of a double from its bits (mantissa truncated,
+// relative error < 2^-23); ok is cleared when |v| is outside the normal float
+// range (zero is exact).
+__device__ __forceinline__ float approx_f(double v, bool &ok)
 {
-    long long q = a / b, r = a % b;
-    if (r != 0 && ((r < 0) != (b < 0))) --q;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e > 127) { ok = false; return __int_as_float(sign | 0x7f7fffffu); }
+    if (e < -126) {
+        if ((b << 1) != 0ull) ok = false;
+        return __int_as_float(sign);
+    }
+    return __int_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// floor(n / d) for d != 0: single precision estimate and exact integer correction
+// when the operands are small, int64 division otherwise.
+__device__ __forceinline__ long long floor_div(long long n, long long d)
+{
+    if (d < 0) { n = -n; d = -d; }
+    if (n > -(1LL << 22) && n < (1LL << 22) && d < (1LL << 22)) {
+        int ni = (int)n, di = (int)d;
+        int q = __float2int_rd(__fdividef((float)ni, (float)di));
+        int r = ni - q * di;
+        while (r < 0) { --q; r += di; }
+        while (r >= di) { ++q; r -= di; }
+        return q;
+    }
+    long long q = n / d, r = n % d;
+    if (r < 0) --q;
     return q;
 }
 
-__device__ __forceinline__ long long ceil_div(long long a, long long b)
-{
-    long long q = a / b, r = a % b;
-    if (r != 0 && ((r < 0) == (b < 0))) ++q;
-    return q;
-}
+__device__ __forceinline__ long long ceil_div(long long n, long long d) { return -floor_div(-n, d); }
 
-__device__ __forceinline__ RowState load_row(const Dev &d, int i)
+__device__ __forceinline__ long long clamp_dd(long long v)
 {
-    int4 v = __ldg(reinterpret_cast<const int4 *>(d.rs) + i);
-    RowState s;
-    s.r = (long long)(((unsigned long long)(unsigned)v.y << 32) | (unsigned)v.x);
-    s.w1 = v.z;
-    s.w2 = v.w;
-    return s;
+    return v > kDdMax ? kDdMax : (v < -kDdMax ? -kDdMax : v);
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -84,89 +116,186 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+__device__ __forceinline__ int4 ld_row16(const RowState *p) { return __ldg(reinterpret_cast<const int4 *>(p)); }
+
+__device__ __forceinline__ long long row_r(const int4 &v)
+{
+    return (long long)(((unsigned long long)(unsigned)v.y << 32) | (unsigned)v.x);
+}
+
+__device__ __forceinline__ double i4_double_lo(const int4 &v)
+{
+    return __longlong_as_double((long long)(((unsigned long long)(unsigned)v.y << 32) | (unsigned)v.x));
+}
+
+__device__ __forceinline__ double i4_double_hi(const int4 &v)
+{
+    return __longlong_as_double((long long)(((unsigned long long)(unsigned)v.w << 32) | (unsigned)v.z));
+}
+
+// Position of the column containing nonzero e (s_ptr: nc + 1 column offsets).
+__device__ __forceinline__ int find_col(const int *s_ptr, int nc, int e)
+{
+    int lo = 0, hi = nc - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Global candidate order: larger score, then lower variable index.
 __device__ __forceinline__ bool cand_better(long long s1, int v1, long long s2, int v2)
 {
     return s1 > s2 || (s1 == s2 && v1 < v2);
 }
 
-__device__ __forceinline__ void warp_reduce_cand(long long &s, int &var, int &dc, double &xh)
+__device__ __forceinline__ void warp_reduce_cand(Cand &c)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        long long s2 = __shfl_xor_sync(FULLMASK, s, o);
-        int v2 = __shfl_xor_sync(FULLMASK, var, o);
-        int d2 = __shfl_xor_sync(FULLMASK, dc, o);
-        double x2 = __shfl_xor_sync(FULLMASK, xh, o);
-        if (cand_better(s2, v2, s, var)) { s = s2; var = v2; dc = d2; xh = x2; }
+        long long s2 = __shfl_xor_sync(FULLMASK, c.s, o);
+        int v2 = __shfl_xor_sync(FULLMASK, c.var, o);
+        int d2 = __shfl_xor_sync(FULLMASK, c.dc, o);
+        double x2 = __shfl_xor_sync(FULLMASK, c.xhat, o);
+        if (cand_better(s2, v2, c.s, c.var)) { c.s = s2; c.var = v2; c.dc = d2; c.xhat = x2; }
     }
 }
 
-// Reduce one candidate per thread to thread 0 of the block; returns it there.
+// Reduce one candidate per thread to thread 0 of the block.
 __device__ Cand block_reduce_cand(Cand c)
 {
     __shared__ Cand red[32];
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    warp_reduce_cand(c.s, c.var, c.dc, c.xhat);
+    warp_reduce_cand(c);
     if (lane == 0) red[warp] = c;
     __syncthreads();
     int nw = (blockDim.x + 31) >> 5;
     if (warp == 0) {
         Cand r = lane < nw ? red[lane] : Cand{0, kNoVar, 0, 0.0};
-        warp_reduce_cand(r.s, r.var, r.dc, r.xhat);
+        warp_reduce_cand(r);
         c = r;
     }
     __syncthreads();
     return c;
 }
 
-// Per-variable candidate order (Eq. best_move ties): larger score, then
-// smaller |t - xbar|, then smaller t.
+// Column being evaluated: keys of xbar and of the bounds, single-precision
+// estimates for the pre-filters, entry ranges.
+struct ColCtx {
+    int j;
+    bool isint;
+    bool fok;              // the single-precision estimates below are usable
+    bool inc_free, dec_free;  // increasing / decreasing x_j is not tabu at this iteration
+    double xb;
+    long long xbi;
+    unsigned long long kxb, kl, ku;
+    long long lo, hi;      // integer: l - xbar, u - xbar (+-2^62 for infinite bounds)
+    float lof, hif;        // integer: the same as floats (+-inf unless |.| < 2^22)
+    float dlf, duf, xaf;   // continuous: estimates of xbar - l, xbar - u (+-inf for infinite bounds), |xbar|
+    int ci0, nI, cf0, nF;
+};
+
+__device__ __forceinline__ ColCtx make_col(const Dev &d, int q, long long iter)
+{
+    ColCtx c;
+    c.j = __ldg(d.var_list + q);
+    const int j = c.j;
+    c.inc_free = iter >= (long long)d.tabu_inc[j];
+    c.dec_free = iter >= (long long)d.tabu_dec[j];
+    c.isint = __ldg(d.vtype + j) != kVarCont;
+    c.xb = d.x[j];
+    const double l = __ldg(d.lb + j), u = __ldg(d.ub + j);
+    const bool fl = isfinite(l), fu = isfinite(u);
+    c.fok = true;
+    if (c.isint) {
+        c.xbi = (long long)c.xb;
+        c.kxb = ikey(c.xbi);
+        const long long li = fl ? (long long)l : LLONG_MIN, ui = fu ? (long long)u : LLONG_MAX;
+        c.kl = ikey(li);
+        c.ku = ikey(ui);
+        c.lo = fl ? li - c.xbi : -(1LL << 62);
+        c.hi = fu ? ui - c.xbi : (1LL << 62);
+        c.lof = c.lo >= -(1LL << 22) ? (float)c.lo : -INFINITY;
+        c.hif = c.hi <= (1LL << 22) ? (float)c.hi : INFINITY;
+        c.dlf = c.duf = c.xaf = 0.0f;
+    } else {
+        c.xbi = 0;
+        c.kxb = dkey(c.xb);
+        c.kl = fl ? dkey(l) : dkey(-1.7976931348623157e308);
+        c.ku = fu ? dkey(u) : dkey(1.7976931348623157e308);
+        c.lo = c.hi = 0;
+        c.lof = c.hif = 0.0f;
+        c.dlf = fl ? approx_f(__dsub_rn(c.xb, l), c.fok) : INFINITY;
+        c.duf = fu ? approx_f(__dsub_rn(c.xb, u), c.fok) : -INFINITY;
+        c.xaf = fabsf(approx_f(c.xb, c.fok));
+    }
+    c.ci0 = __ldg(d.ci_ptr + q);
+    c.nI = __ldg(d.ci_ptr + q + 1) - c.ci0;
+    c.cf0 = __ldg(d.cf_ptr + q);
+    c.nF = __ldg(d.cf_ptr + q + 1) - c.cf0;
+    return c;
+}
+
+__device__ __forceinline__ double key_value(const ColCtx &c, unsigned long long k)
+{
+    return c.isint ? (double)ikey_val(k) : dkey_val(k);
+}
+
+// Per-variable candidate; order (Eq. best_move ties): larger score, then smaller
+// |t - xbar|, then smaller t.  Distances are only computed on score ties.
 struct VCand {
     long long s;
-    double t;
+    unsigned long long key;
     int dc;
     int valid;
 };
 
-__device__ __forceinline__ bool vc_better(const VCand &a, const VCand &b, double xb)
+__device__ __forceinline__ bool vc_better(const VCand &a, const VCand &b, const ColCtx &c)
 {
     if (!a.valid) return false;
     if (!b.valid) return true;
     if (a.s != b.s) return a.s > b.s;
-    double da = fabs(a.t - xb), db = fabs(b.t - xb);
-    if (da != db) return da < db;
-    return a.t < b.t;
+    if (c.isint) {
+        long long ta = ikey_val(a.key), tb = ikey_val(b.key);
+        unsigned long long da = (unsigned long long)(ta > c.xbi ? ta - c.xbi : c.xbi - ta);
+        unsigned long long db = (unsigned long long)(tb > c.xbi ? tb - c.xbi : c.xbi - tb);
+        if (da != db) return da < db;
+    } else {
+        double da = fabs(__dsub_rn(dkey_val(a.key), c.xb)), db = fabs(__dsub_rn(dkey_val(b.key), c.xb));
+        if (da != db) return dkey(da) < dkey(db);
+    }
+    return a.key < b.key;
 }
 
-__device__ __forceinline__ void warp_reduce_vc(VCand &c, double xb)
+__device__ __forceinline__ void warp_reduce_vc(VCand &v, const ColCtx &c)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         VCand p;
-        p.s = __shfl_xor_sync(FULLMASK, c.s, o);
-        p.t = __shfl_xor_sync(FULLMASK, c.t, o);
-        p.dc = __shfl_xor_sync(FULLMASK, c.dc, o);
-        p.valid = __shfl_xor_sync(FULLMASK, c.valid, o);
-        if (vc_better(p, c, xb)) c = p;
+        p.s = __shfl_xor_sync(FULLMASK, v.s, o);
+        p.key = __shfl_xor_sync(FULLMASK, v.key, o);
+        p.dc = __shfl_xor_sync(FULLMASK, v.dc, o);
+        p.valid = __shfl_xor_sync(FULLMASK, v.valid, o);
+        if (vc_better(p, v, c)) v = p;
     }
 }
 
-__device__ VCand block_reduce_vc(VCand c, double xb)
+__device__ VCand block_reduce_vc(VCand v, const ColCtx &c)
 {
     __shared__ VCand red[32];
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    warp_reduce_vc(c, xb);
-    if (lane == 0) red[warp] = c;
+    warp_reduce_vc(v, c);
+    if (lane == 0) red[warp] = v;
     __syncthreads();
     int nw = (blockDim.x + 31) >> 5;
     if (warp == 0) {
-        VCand r = lane < nw ? red[lane] : VCand{0, 0.0, 0, 0};
-        warp_reduce_vc(r, xb);
-        c = r;
+        VCand r = lane < nw ? red[lane] : VCand{0, 0ull, 0, 0};
+        warp_reduce_vc(r, c);
+        v = r;
     }
     __syncthreads();
-    return c;
+    return v;
 }
 
 // Admissibility under tabu and aspiration.
@@ -174,159 +303,213 @@ __device__ __forceinline__ bool admissible(bool increase, int j, int dc, const D
                                            long long nviol, long long bestnv)
 {
     int stamp = increase ? d.tabu_inc[j] : d.tabu_dec[j];
-    bool tabu = iter < (long long)stamp;
-    return !tabu || (nviol + (long long)dc < bestnv);
+    return iter >= (long long)stamp || (nviol + (long long)dc < bestnv);
+}
+
+// A candidate of column c at key k with score sg and count change dcv:
+// admissible when its direction is not tabu, or by aspiration.
+__device__ __forceinline__ void consider(VCand &vb, const ColCtx &c, unsigned long long k, long long sg, int dcv,
+                                         long long nviol, long long bestnv)
+{
+    if (k == c.kxb) return;
+    const bool inc = k > c.kxb;
+    if (!((inc ? c.inc_free : c.dec_free) || nviol + (long long)dcv < bestnv)) return;
+    const VCand n{sg, k, dcv, 1};
+    if (vc_better(n, vb, c)) vb = n;
 }
 
 // Column result -> optional per-variable outputs and the caller's running best.
-__device__ __forceinline__ void finish_column(const Dev &d, const VarOut &o, int j, double xb, const VCand &b,
+__device__ __forceinline__ void finish_column(const Dev &d, const VarOut &o, const ColCtx &c, const VCand &b,
                                               Cand &best)
 {
     bool mv = b.valid && b.s > 0;
-    if (o.xhat) o.xhat[j] = mv ? b.t : xb;
-    if (o.s) o.s[j] = mv ? b.s : 0;
-    if (o.dc) o.dc[j] = mv ? b.dc : 0;
-    if (mv && cand_better(b.s, j, best.s, best.var)) best = Cand{b.s, j, b.dc, b.t};
+    double xh = mv ? key_value(c, b.key) : c.xb;
+    if (o.xhat) o.xhat[c.j] = xh;
+    if (o.s) o.s[c.j] = mv ? b.s : 0;
+    if (o.dc) o.dc[c.j] = mv ? b.dc : 0;
+    if (mv && cand_better(b.s, c.j, best.s, best.var)) best = Cand{b.s, c.j, b.dc, xh};
+}
+
+__device__ __forceinline__ bool gated_done(const Dev &d, int gate)
+{
+    return gate && *(volatile int *)&d.ctl->done;
 }
 
 // ------------------------------------------------------- binary flip scoring
 
-// Penalty of a flip on one normalised half with integer residual r and signed
-// coefficient change ad = a * (new - old) (Sec. 3.1, Scoring Functions).
+// Penalty of moving one normalised half by ad = a * (new - old) (Sec. 3.1,
+// Scoring Functions), integral row with int64 residual r.
 __device__ __forceinline__ void flip_int(long long r, long long ad, long long w, long long &s, int &dc)
 {
-    long long r1 = r + ad;
-    bool v0 = r > 0, v1 = r1 > 0;
+    const long long r1 = r + ad;
+    const bool v0 = r > 0, v1 = r1 > 0;
     if (!v0 && v1) s -= 2 * w;
     else if (v0 && !v1) s += 2 * w;
     else if (v0 && v1) s += (ad < 0) ? w : -w;
     dc += (int)v1 - (int)v0;
 }
 
-__device__ __forceinline__ void flip_fp(double r, double ad, double eps, long long w, long long &s, int &dc)
+// Same on a non-integral row from its margin m = eps - r: violated <=> m < 0,
+// violated after the move <=> ad > m.
+__device__ __forceinline__ void flip_fp(double ad, double m, long long w, long long &s, int &dc)
 {
-    double r1 = __dadd_rn(r, ad);
-    bool v0 = r > eps, v1 = r1 > eps;
+    const bool v0 = dneg(m), v1 = dgt(ad, m);
     if (!v0 && v1) s -= 2 * w;
     else if (v0 && !v1) s += 2 * w;
-    else if (v0 && v1) s += (ad < 0.0) ? w : -w;
+    else if (v0 && v1) s += dneg(ad) ? w : -w;
     dc += (int)v1 - (int)v0;
 }
 
-// Partial flip score of column j over the lanes sub, sub+G, ...
-__device__ __forceinline__ void bin_col_partial(const Dev &d, int j, bool up, int sub, int G, long long &s, int &dc)
+// One CSC part of a binary tile: every thread takes aligned groups of 8
+// consecutive nonzeros (two 16-byte loads of row indices, two or four of
+// coefficients), gathers their row states together and scores the flips into
+// per-column accumulators in shared memory.
+template <bool FP>
+__device__ __forceinline__ void bin_part(const Dev &d, int nc, const int *s_ptr, const unsigned char *s_up,
+                                         long long *s_acc, int *s_dc)
 {
-    int e0 = __ldg(d.ci_ptr + j), e1 = __ldg(d.ci_ptr + j + 1);
-    for (int e = e0 + sub; e < e1; e += G) {
-        int i = __ldg(d.ci_row + e);
-        long long a = __ldg(d.ci_val + e);
-        RowState st = load_row(d, i);
-        long long ad = up ? a : -a;
-        flip_int(st.r, ad, st.w1, s, dc);
-        if (st.w2 >= 0) flip_int(-st.r, -ad, st.w2, s, dc);
-    }
-    int f0 = __ldg(d.cf_ptr + j), f1 = __ldg(d.cf_ptr + j + 1);
-    for (int e = f0 + sub; e < f1; e += G) {
-        int i = __ldg(d.cf_row + e);
-        double a = __ldg(d.cf_val + e);
-        RowState st = load_row(d, i);
-        double eps = __ldg(d.eps + i);
-        double r = __longlong_as_double(st.r);
-        double ad = up ? a : -a;
-        flip_fp(r, ad, eps, st.w1, s, dc);
-        if (st.w2 >= 0) flip_fp(-r, -ad, eps, st.w2, s, dc);
+    const int E0 = s_ptr[0], E1 = s_ptr[nc];
+    const int g1 = (E1 + 7) >> 3;
+    for (int g = (E0 >> 3) + threadIdx.x; g < g1; g += blockDim.x) {
+        const int eb = g << 3;
+        int rows[8];
+        {
+            const int4 *rp = reinterpret_cast<const int4 *>((FP ? d.cf_row : d.ci_row) + eb);
+            const int4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+            rows[0] = r0.x; rows[1] = r0.y; rows[2] = r0.z; rows[3] = r0.w;
+            rows[4] = r1.x; rows[5] = r1.y; rows[6] = r1.z; rows[7] = r1.w;
+        }
+        double dv[8];
+        int iv[8];
+        if (FP) {
+            const double2 *vp = reinterpret_cast<const double2 *>(d.cf_val + eb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { const double2 v = __ldg(vp + k); dv[2 * k] = v.x; dv[2 * k + 1] = v.y; }
+        } else {
+            const int4 *vp = reinterpret_cast<const int4 *>(d.ci_val + eb);
+            const int4 v0 = __ldg(vp), v1 = __ldg(vp + 1);
+            iv[0] = v0.x; iv[1] = v0.y; iv[2] = v0.z; iv[3] = v0.w;
+            iv[4] = v1.x; iv[5] = v1.y; iv[6] = v1.z; iv[7] = v1.w;
+        }
+        int col = find_col(s_ptr, nc, max(eb, E0));
+        long long acc = 0;
+        int accd = 0;
+        constexpr int B = FP ? 4 : 8;
+#pragma unroll
+        for (int b0 = 0; b0 < 8; b0 += B) {
+            int4 st0[B], st1[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int e = eb + b0 + q;
+                if (e >= E0 && e < E1) {
+                    const int4 *pp = reinterpret_cast<const int4 *>(d.rs + rows[b0 + q]);
+                    st0[q] = __ldg(pp);
+                    if (FP) st1[q] = __ldg(pp + 1);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int e = eb + b0 + q;
+                if (e < E0 || e >= E1) continue;
+                while (s_ptr[col + 1] <= e) {
+                    if (acc | accd) {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(s_acc + col), (unsigned long long)acc);
+                        atomicAdd(s_dc + col, accd);
+                    }
+                    acc = 0;
+                    accd = 0;
+                    ++col;
+                }
+                const bool up = s_up[col] != 0;
+                if (FP) {
+                    const double ad = up ? dv[b0 + q] : dflip(dv[b0 + q]);
+                    flip_fp(ad, i4_double_lo(st1[q]), st0[q].z, acc, accd);
+                    if (st0[q].w >= 0) flip_fp(dflip(ad), i4_double_hi(st1[q]), st0[q].w, acc, accd);
+                } else {
+                    const long long ad = up ? (long long)iv[b0 + q] : -(long long)iv[b0 + q];
+                    const long long r = row_r(st0[q]);
+                    flip_int(r, ad, st0[q].z, acc, accd);
+                    if (st0[q].w >= 0) flip_int(-r, -ad, st0[q].w, acc, accd);
+                }
+            }
+        }
+        if (acc | accd) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(s_acc + col), (unsigned long long)acc);
+            atomicAdd(s_dc + col, accd);
+        }
     }
 }
 
-template <int G>
-__device__ void eval_bin_tile(const Dev &d, const Tile &tl, const VarOut &o, long long iter, long long nviol,
-                              long long bestnv, Cand &best)
+// Binary columns at positions [tile.begin, tile.end): their nonzeros are
+// contiguous in both CSC matrices, so the tile streams two flat ranges.
+__global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, const Tile *tiles, VarOut o, int gate)
 {
-    const int groups = kEvalThreads / G;
-    int g = threadIdx.x / G, sub = threadIdx.x % G;
-    int count = tl.end - tl.begin;
-    int rounds = (count + groups - 1) / groups;
-    for (int rd = 0; rd < rounds; ++rd) {
-        int q = rd * groups + g;
-        bool active = q < count;
-        int j = active ? __ldg(d.var_list + tl.begin + q) : 0;
-        long long s = 0;
-        int dc = 0;
-        double xb = 0.0;
-        bool up = true;
-        if (active) {
-            xb = d.x[j];
-            up = xb == 0.0;
-            bin_col_partial(d, j, up, sub, G, s, dc);
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            s += __shfl_xor_sync(FULLMASK, s, off, G);
-            dc += __shfl_xor_sync(FULLMASK, dc, off, G);
-        }
-        if (active && sub == 0) {
-            VCand b{s, up ? 1.0 : 0.0, dc, 0};
-            b.valid = admissible(up, j, dc, d, iter, nviol, bestnv) ? 1 : 0;
-            finish_column(d, o, j, xb, b, best);
-        }
+    if (gated_done(d, gate)) return;
+    __shared__ int s_pi[kBinMaxCols + 1];
+    __shared__ int s_pf[kBinMaxCols + 1];
+    __shared__ long long s_acc[kBinMaxCols];
+    __shared__ int s_dc[kBinMaxCols];
+    __shared__ unsigned char s_up[kBinMaxCols];
+    const Tile tl = tiles[blockIdx.x];
+    const int q0 = tl.begin, nc = tl.end - tl.begin;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        s_acc[c] = 0;
+        s_dc[c] = 0;
+        s_up[c] = __double_as_longlong(d.x[__ldg(d.var_list + q0 + c)]) == 0;  // flip 0 -> 1
     }
-}
-
-__device__ void eval_bin_cta(const Dev &d, const Tile &tl, const VarOut &o, long long iter, long long nviol,
-                             long long bestnv, Cand &best)
-{
-    int j = __ldg(d.var_list + tl.begin);
-    double xb = d.x[j];
-    bool up = xb == 0.0;
-    long long s = 0;
-    int dc = 0;
-    bin_col_partial(d, j, up, threadIdx.x, blockDim.x, s, dc);
-    __shared__ long long rs_[32];
-    __shared__ int rc_[32];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        s += __shfl_xor_sync(FULLMASK, s, off);
-        dc += __shfl_xor_sync(FULLMASK, dc, off);
-    }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { rs_[warp] = s; rc_[warp] = dc; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long ts = 0;
-        int tc = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ts += rs_[w]; tc += rc_[w]; }
-        VCand b{ts, up ? 1.0 : 0.0, tc, 0};
-        b.valid = admissible(up, j, tc, d, iter, nviol, bestnv) ? 1 : 0;
-        finish_column(d, o, j, xb, b, best);
+    for (int c = threadIdx.x; c <= nc; c += blockDim.x) {
+        s_pi[c] = __ldg(d.ci_ptr + q0 + c);
+        s_pf[c] = __ldg(d.cf_ptr + q0 + c);
     }
     __syncthreads();
+    bin_part<false>(d, nc, s_pi, s_up, s_acc, s_dc);
+    bin_part<true>(d, nc, s_pf, s_up, s_acc, s_dc);
+    __syncthreads();
+    const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
+    Cand best{0, kNoVar, 0, 0.0};
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int j = __ldg(d.var_list + q0 + c);
+        const bool up = s_up[c] != 0;
+        const long long sc = s_acc[c];
+        const int dc = s_dc[c];
+        bool mv = sc > 0;
+        if (mv) {
+            const int stamp = up ? d.tabu_inc[j] : d.tabu_dec[j];
+            mv = iter >= (long long)stamp || nviol + (long long)dc < bestnv;
+        }
+        const double xh = up ? 1.0 : 0.0;
+        if (o.xhat) o.xhat[j] = mv ? xh : d.x[j];
+        if (o.s) o.s[j] = mv ? sc : 0;
+        if (o.dc) o.dc[j] = mv ? dc : 0;
+        if (mv && cand_better(sc, j, best.s, best.var)) best = Cand{sc, j, dc, xh};
+    }
+    const Cand b = block_reduce_cand(best);
+    if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
 }
 
 // ---------------------------------------------- breakpoint generation (Alg. 1)
 
-// Scalars of Algorithm 1: beta (score as x -> -inf), alpha (adjustment right of
-// xbar) and their count-lane twins, all in half-weight / row units.
+// Scalars of Algorithm 1 in half-weight units: beta (score as x -> -inf),
+// alpha (added right of xbar) and their violation-count twins.
 struct Acc {
     long long beta, alpha;
     int beta_c, alpha_c;
 };
 
-// Entries produced by one normalised half of a nonzero.
-//  type 1: (t, -1, +D, count -1)            rows with a < 0 (need x >= t)
-//  type 2: (t, -1, 0, 0), (t, +1, D, +1)    rows with a > 0 (need x <= t)
+// Entry of one normalised half: type 1 "pre" (a < 0: delta D counts from t on,
+// violation count -1), type 2 "post" (a > 0: t is a candidate, D counts right of
+// t, violation count +1), type 0 none.
 struct Half {
-    double t;
+    unsigned long long key;
     long long D;
     int type;
 };
 
-__device__ __forceinline__ int half_count(const Half &h) { return h.type; }
-
-// Case table of Algorithm 1 in half units: the row's state at xbar (violated,
-// satisfied, tight) decides beta/alpha and the entries; entries left of l are
-// folded into beta, entries right of u are dropped.
-__device__ __forceinline__ void half_case(bool viol, bool tight, bool apos, double t, long long w, double l,
-                                          double u, Acc &acc, Half &h)
+// Case table of Algorithm 1 for one normalised half (half-weight units).  The
+// entry lands left of l (side -1: folded into beta), right of u (side +1:
+// dropped) or at key (side 0, compared with the bound keys here).
+__device__ __forceinline__ void half_case(bool viol, bool tight, bool apos, int side, unsigned long long key,
+                                          long long w, const ColCtx &c, Acc &acc, Half &h)
 {
     h.type = 0;
     if (tight) {
@@ -345,90 +528,139 @@ __device__ __forceinline__ void half_case(bool viol, bool tight, bool apos, doub
         else { D = -2 * w; }
         type = 2;
     }
-    if (t < l) {
+    if (side == 0) side = key < c.kl ? -1 : (key > c.ku ? 1 : 0);
+    if (side < 0) {
         acc.beta += D;
         acc.beta_c += (type == 1) ? -1 : 1;
         return;
     }
-    if (t > u) return;
-    h.t = t;
+    if (side > 0) return;
+    h.key = key;
     h.D = D;
     h.type = type;
 }
 
-// Integral row, integer variable: exact integer breakpoint offset.
-__device__ __forceinline__ void int_half(long long r, long long a, long long w, double xb, double l, double u,
-                                         Acc &acc, Half &h)
+// Integral row (integer variable).  The breakpoint xbar + floor(-r/a) (a > 0)
+// or xbar + ceil(-r/a) (a < 0) is compared with the bounds by exact int64
+// products first (|lo a|, |hi a| <= 2^53 on integral rows); the division runs
+// only for breakpoints inside [l, u].
+__device__ __forceinline__ void int_half(long long r, long long a, long long w, const ColCtx &c, Acc &acc, Half &h)
 {
-    bool viol = r > 0;
-    long long dd = (a > 0) ? floor_div(-r, a) : ceil_div(-r, a);
-    bool tight = !viol && dd == 0;
-    double t = __dadd_rn(xb, (double)dd);
-    half_case(viol, tight, a > 0, t, w, l, u, acc, h);
-}
-
-// Non-integral row.  Continuous variable: t = xbar - r / a (the row becomes
-// tight); integer variable: the last integer at which the row is satisfied
-// within eps, xbar + floor((eps - r) / a) for a > 0 (ceil for a < 0).
-__device__ __forceinline__ void fp_half(double r, double a, double eps, long long w, double xb, bool isint,
-                                        double l, double u, Acc &acc, Half &h)
-{
-    bool viol = r > eps;
-    double t;
-    bool tight;
-    if (isint) {
-        double q = __ddiv_rn(__dsub_rn(eps, r), a);
-        double dd = (a > 0.0) ? floor(q) : ceil(q);
-        t = __dadd_rn(xb, dd);
-        tight = !viol && dd == 0.0;
-    } else {
-        double q = __ddiv_rn(r, a);
-        t = __dsub_rn(xb, q);
-        tight = !viol && (fabs(r) <= eps || t == xb);
+    const bool viol = r > 0;
+    const bool apos = a > 0;
+    int side;
+    if (apos) side = (r > -c.lo * a) ? -1 : ((-r >= (c.hi + 1) * a) ? 1 : 0);
+    else side = (-r >= (c.lo - 1) * a) ? -1 : ((-r < c.hi * a) ? 1 : 0);
+    if (side != 0) {
+        half_case(viol, false, apos, side, 0ull, w, c, acc, h);
+        return;
     }
-    t = __dadd_rn(t, 0.0);
-    half_case(viol, tight, a > 0.0, t, w, l, u, acc, h);
+    const long long dd = apos ? floor_div(-r, a) : ceil_div(-r, a);
+    half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
 }
 
-// Both halves of one nonzero of column j.  v < nI indexes the integral part
-// (ci_*), otherwise v - nI the non-integral part (cf_*).
-__device__ __forceinline__ void gen_entry(const Dev &d, int ci0, int cf0, int nI, int v, double xb, bool isint,
-                                          double l, double u, Acc &acc, Half &h1, Half &h2)
+// |x| with a relative error bound e and an absolute floor, for the certain
+// comparisons below: x < y is certain when x + slack(x) < y - slack(y).
+__device__ __forceinline__ float slack(float x) { return fabsf(x) * 1.0e-5f + 1.0e-30f; }
+
+// Integer variable on a non-integral row with margin m = eps - r: the
+// breakpoint is xbar + floor(m / a) (a > 0) or xbar + ceil(m / a) (a < 0).
+// Returns the side (-1 left of l, +1 right of u) when single-precision
+// products decide it, else 0.
+__device__ __forceinline__ int int_fp_side(double m, double a, bool apos, const ColCtx &c)
+{
+    bool ok = true;
+    const float mf = approx_f(m, ok), af = approx_f(a, ok);
+    if (!ok) return 0;
+    if (apos) {
+        const float P = c.lof * af;              // t < l  <=>  m < lo a
+        if (mf + slack(mf) < P - slack(P)) return -1;
+        const float Q = (c.hif + 1.0f) * af;     // t > u  <=>  m >= (hi + 1) a
+        if (mf - slack(mf) > Q + slack(Q)) return 1;
+    } else {
+        const float P = (c.lof - 1.0f) * af;     // t < l  <=>  m >= (lo - 1) a
+        if (mf - slack(mf) > P + slack(P)) return -1;
+        const float Q = c.hif * af;              // t > u  <=>  m < hi a
+        if (mf + slack(mf) < Q - slack(Q)) return 1;
+    }
+    return 0;
+}
+
+// Continuous variable: side of t = xbar - r / a (t < l <=> r/a > xbar - l,
+// t > u <=> r/a < xbar - u), decided from single-precision products with a
+// margin that also covers the rounding of t itself; else 0.
+__device__ __forceinline__ int cont_fp_side(double r, double a, bool apos, const ColCtx &c)
+{
+    bool ok = c.fok;
+    const float rf = approx_f(r, ok), af = approx_f(a, ok);
+    if (!ok) return 0;
+    const float tol = c.xaf * fabsf(af) * 1.0e-10f;
+    const float P = c.dlf * af, Q = c.duf * af;
+    if (apos) {
+        if (rf - slack(rf) - tol > P + slack(P)) return -1;
+        if (rf + slack(rf) + tol < Q - slack(Q)) return 1;
+    } else {
+        if (rf + slack(rf) + tol < P - slack(P)) return -1;
+        if (rf - slack(rf) - tol > Q + slack(Q)) return 1;
+    }
+    return 0;
+}
+
+// Non-integral row, one half with residual r, coefficient a and margins
+// m = eps - r (own), mo = eps + r (other half).  Integer variable: the last
+// integer at which the row is satisfied within eps.  Continuous variable:
+// t = xbar - r / a (the row becomes tight); tight when |r| <= eps or t == xbar.
+// The double division runs only when the side test cannot place t outside [l, u].
+__device__ __forceinline__ void fp_half(double r, double a, double m, double mo, long long w, const ColCtx &c,
+                                        Acc &acc, Half &h)
+{
+    const bool viol = dneg(m);
+    const bool apos = !dneg(a);
+    if (c.isint) {
+        const int side = int_fp_side(m, a, apos, c);
+        if (side != 0) {
+            half_case(viol, false, apos, side, 0ull, w, c, acc, h);
+            return;
+        }
+        const double q = __ddiv_rn(m, a);
+        const long long dd = clamp_dd(apos ? __double2ll_rd(q) : __double2ll_ru(q));
+        half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
+    } else {
+        const bool near0 = !viol && !dneg(mo);  // |r| <= eps
+        const int side = cont_fp_side(r, a, apos, c);
+        if (side != 0) {
+            half_case(viol, near0, apos, side, 0ull, w, c, acc, h);
+            return;
+        }
+        const double t = __dsub_rn(c.xb, __ddiv_rn(r, a));
+        unsigned long long k = dkey(t);
+        if (k == dkey(-0.0)) k = dkey(0.0);
+        half_case(viol, near0 || (!viol && k == c.kxb), apos, 0, k, w, c, acc, h);
+    }
+}
+
+// Both halves of the v-th nonzero of the column (integral part first).
+__device__ __forceinline__ void gen_entry(const Dev &d, const ColCtx &c, int v, Acc &acc, Half &h1, Half &h2)
 {
     h1.type = 0;
     h2.type = 0;
-    if (v < nI) {
-        int e = ci0 + v;
-        int i = __ldg(d.ci_row + e);
-        long long a = __ldg(d.ci_val + e);
-        RowState st = load_row(d, i);
-        int_half(st.r, a, st.w1, xb, l, u, acc, h1);
-        if (st.w2 >= 0) int_half(-st.r, -a, st.w2, xb, l, u, acc, h2);
+    if (v < c.nI) {
+        const int e = c.ci0 + v;
+        const int i = __ldg(d.ci_row + e);
+        const long long a = __ldg(d.ci_val + e);
+        const int4 st = ld_row16(d.rs + i);
+        const long long r = row_r(st);
+        int_half(r, a, st.z, c, acc, h1);
+        if (st.w >= 0) int_half(-r, -a, st.w, c, acc, h2);
     } else {
-        int e = cf0 + (v - nI);
-        int i = __ldg(d.cf_row + e);
-        double a = __ldg(d.cf_val + e);
-        RowState st = load_row(d, i);
-        double eps = __ldg(d.eps + i);
-        double r = __longlong_as_double(st.r);
-        fp_half(r, a, eps, st.w1, xb, isint, l, u, acc, h1);
-        if (st.w2 >= 0) fp_half(-r, -a, eps, st.w2, xb, isint, l, u, acc, h2);
-    }
-}
-
-// aux word of a sort entry: bit 31 = marker (+1), bits 0..1 = count delta + 1.
-__device__ __forceinline__ unsigned make_aux(int plus, int dc) { return ((unsigned)plus << 31) | (unsigned)(dc + 1); }
-__device__ __forceinline__ int aux_dc(unsigned a) { return (int)(a & 3u) - 1; }
-__device__ __forceinline__ unsigned aux_plus(unsigned a) { return a >> 31; }
-
-__device__ __forceinline__ void put_half(const Half &h, int pos, unsigned long long *k, long long *dl, unsigned *ax)
-{
-    if (h.type == 1) {
-        k[pos] = ord_key(h.t); dl[pos] = h.D; ax[pos] = make_aux(0, -1);
-    } else if (h.type == 2) {
-        unsigned long long kk = ord_key(h.t);
-        k[pos] = kk; dl[pos] = 0; ax[pos] = make_aux(0, 0);
-        k[pos + 1] = kk; dl[pos + 1] = h.D; ax[pos + 1] = make_aux(1, 1);
+        const int e = c.cf0 + (v - c.nI);
+        const int i = __ldg(d.cf_row + e);
+        const double a = __ldg(d.cf_val + e);
+        const int4 *p = reinterpret_cast<const int4 *>(d.rs + i);
+        const int4 s0 = __ldg(p), s1 = __ldg(p + 1);
+        const double r = i4_double_lo(s0), m1 = i4_double_lo(s1), m2 = i4_double_hi(s1);
+        fp_half(r, a, m1, m2, s0.z, c, acc, h1);
+        if (s0.w >= 0) fp_half(dflip(r), dflip(a), m2, m1, s0.w, c, acc, h2);
     }
 }
 
@@ -443,13 +675,287 @@ __device__ __forceinline__ void warp_allreduce_acc(Acc &a)
     }
 }
 
-// Lexicographic (t, marker) order of sort entries.
-__device__ __forceinline__ bool entry_less(unsigned long long k1, unsigned a1, unsigned long long k2, unsigned a2)
+// aux word of a sort entry: bit 31 = post marker, bits 0..1 = count delta + 1.
+__device__ __forceinline__ unsigned make_aux(int post, int dc) { return ((unsigned)post << 31) | (unsigned)(dc + 1); }
+__device__ __forceinline__ int aux_dc(unsigned a) { return (int)(a & 3u) - 1; }
+__device__ __forceinline__ unsigned aux_post(unsigned a) { return a >> 31; }
+
+__device__ __forceinline__ void put_half(const Half &h, int pos, unsigned long long *k, long long *dl, unsigned *ax)
 {
-    return k1 < k2 || (k1 == k2 && aux_plus(a1) < aux_plus(a2));
+    k[pos] = h.key;
+    dl[pos] = h.D;
+    ax[pos] = h.type == 1 ? make_aux(0, -1) : make_aux(1, 1);
 }
 
-// ------------------------------------------- warp sort / scan / argmax (K/lane)
+// Lexicographic (t, marker) order: pre entries before post entries at equal t.
+__device__ __forceinline__ bool entry_less(unsigned long long k1, unsigned a1, unsigned long long k2, unsigned a2)
+{
+    return k1 < k2 || (k1 == k2 && aux_post(a1) < aux_post(a2));
+}
+
+// Candidate test of a sorted entry given its neighbours (Algorithm 1, phase 4):
+// the last pre entry of an equal-t run, or a post entry that opens its run.
+__device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, unsigned long long kprev, bool has_prev,
+                                             unsigned long long knext, unsigned anext)
+{
+    if (k == kPadKey) return false;
+    if (aux_post(a) == 0) return knext != k || aux_post(anext) != 0;
+    return !has_prev || kprev != k;
+}
+
+// ------------------------------------------- flat tiles of non-binary columns
+//
+// A tile is a run of consecutive positions (columns contiguous in both CSC
+// matrices).  All threads of the CTA stream the tile's nonzeros in aligned
+// groups of 8 (two 16-byte loads of row indices and coefficients per thread,
+// the row states of the group gathered together), generate the breakpoint
+// entries of Algorithm 1 and append the ones inside [l, u] to the column's
+// segment in shared memory.  Then each column's segment is sorted, scanned and
+// reduced: short segments by bitonic networks packed several to a warp (8 or
+// 16 lanes per column), longer ones by a whole warp with K entries per lane.
+
+struct TileCol {
+    ColCtx c;
+    long long beta, alpha;
+    int beta_c, alpha_c;
+    int cnt;          // entries in the column's list
+    int pad;
+    long long lbase;  // offset of the column's list in the scratch
+};
+
+using SEnt = SEntry;
+
+__device__ __forceinline__ void flush_acc(TileCol &t, Acc &a)
+{
+    if (a.beta) atomicAdd(reinterpret_cast<unsigned long long *>(&t.beta), (unsigned long long)a.beta);
+    if (a.alpha) atomicAdd(reinterpret_cast<unsigned long long *>(&t.alpha), (unsigned long long)a.alpha);
+    if (a.beta_c) atomicAdd(&t.beta_c, a.beta_c);
+    if (a.alpha_c) atomicAdd(&t.alpha_c, a.alpha_c);
+    a = Acc{0, 0, 0, 0};
+}
+
+// Exact breakpoint of one half whose side could not be decided by products.
+__device__ __forceinline__ void int_half_exact(long long r, long long a, long long w, const ColCtx &c, Acc &acc, Half &h)
+{
+    const bool viol = r > 0;
+    const bool apos = a > 0;
+    const long long dd = apos ? floor_div(-r, a) : ceil_div(-r, a);
+    half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
+}
+
+__device__ __forceinline__ void fp_half_exact(double r, double a, double m, double mo, long long w, const ColCtx &c,
+                                              Acc &acc, Half &h)
+{
+    const bool viol = dneg(m);
+    const bool apos = !dneg(a);
+    if (c.isint) {
+        const double q = __ddiv_rn(m, a);
+        const long long dd = clamp_dd(apos ? __double2ll_rd(q) : __double2ll_ru(q));
+        half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
+    } else {
+        const bool near0 = !viol && !dneg(mo);
+        const double t = __dsub_rn(c.xb, __ddiv_rn(r, a));
+        unsigned long long k = dkey(t);
+        if (k == dkey(-0.0)) k = dkey(0.0);
+        half_case(viol, near0 || (!viol && k == c.kxb), apos, 0, k, w, c, acc, h);
+    }
+}
+
+// Algorithm 1 scalars of a half whose breakpoint is decided without its key:
+// tight, or certainly left of l (side -1) / right of u (side +1).
+__device__ __forceinline__ void half_acc(bool viol, bool tight, bool apos, int side, long long w, Acc &acc)
+{
+    if (tight) {
+        if (apos) { acc.alpha -= 2 * w; acc.alpha_c += 1; }
+        else { acc.beta -= 2 * w; acc.alpha += 2 * w; acc.beta_c += 1; acc.alpha_c -= 1; }
+        return;
+    }
+    long long D;
+    if (!apos) {
+        if (viol) { acc.beta -= w; acc.alpha += 2 * w; D = w; }
+        else { acc.beta -= 2 * w; acc.beta_c += 1; D = 2 * w; }
+        if (side < 0) { acc.beta += D; acc.beta_c -= 1; }
+    } else {
+        if (viol) { acc.beta += 2 * w; acc.alpha -= 2 * w; acc.beta_c -= 1; D = -w; }
+        else { D = -2 * w; }
+        if (side < 0) { acc.beta += D; acc.beta_c += 1; }
+    }
+}
+
+// What the classification needs of a column (kept in registers while streaming).
+struct ClsCtx {
+    long long lo, hi;
+    float lof, hif, dlf, duf, xaf;
+    bool isint, fok;
+};
+
+__device__ __forceinline__ ClsCtx cls_of(const ColCtx &c)
+{
+    return ClsCtx{c.lo, c.hi, c.lof, c.hif, c.dlf, c.duf, c.xaf, c.isint, c.fok};
+}
+
+// Cheap classification of one half (products only).  Returns true when the
+// half needs its exact breakpoint; otherwise its Algorithm 1 scalars are added.
+__device__ __forceinline__ bool classify_int(long long r, long long a, long long w, const ClsCtx &c, Acc &acc)
+{
+    const bool viol = r > 0;
+    const bool apos = a > 0;
+    int side;
+    if (apos) side = (r > -c.lo * a) ? -1 : ((-r >= (c.hi + 1) * a) ? 1 : 0);
+    else side = (-r >= (c.lo - 1) * a) ? -1 : ((-r < c.hi * a) ? 1 : 0);
+    if (side == 0) return true;
+    half_acc(viol, false, apos, side, w, acc);
+    return false;
+}
+
+__device__ __forceinline__ bool classify_fp(double r, double a, double m, double mo, long long w, const ClsCtx &c,
+                                            Acc &acc)
+{
+    const bool viol = dneg(m);
+    const bool apos = !dneg(a);
+    bool ok = true;
+    const float af = approx_f(a, ok);
+    int side = 0;
+    if (c.isint) {
+        const float mf = approx_f(m, ok);
+        if (ok) {
+            if (apos) {
+                const float P = c.lof * af, Q = (c.hif + 1.0f) * af;  // t < l <=> m < lo a; t > u <=> m >= (hi+1) a
+                if (mf + slack(mf) < P - slack(P)) side = -1;
+                else if (mf - slack(mf) > Q + slack(Q)) side = 1;
+            } else {
+                const float P = (c.lof - 1.0f) * af, Q = c.hif * af;  // t < l <=> m >= (lo-1) a; t > u <=> m < hi a
+                if (mf - slack(mf) > P + slack(P)) side = -1;
+                else if (mf + slack(mf) < Q - slack(Q)) side = 1;
+            }
+        }
+        if (side == 0) return true;
+        half_acc(viol, false, apos, side, w, acc);
+        return false;
+    }
+    if (!viol && !dneg(mo)) {  // |r| <= eps: tight whatever t is
+        half_acc(false, true, apos, 0, w, acc);
+        return false;
+    }
+    ok = ok && c.fok;
+    const float rf = approx_f(r, ok);
+    if (ok) {
+        const float tol = c.xaf * fabsf(af) * 1.0e-10f;
+        const float P = c.dlf * af, Q = c.duf * af;  // t < l <=> r/a > xbar - l; t > u <=> r/a < xbar - u
+        if (apos) {
+            if (rf - slack(rf) - tol > P + slack(P)) side = -1;
+            else if (rf + slack(rf) + tol < Q - slack(Q)) side = 1;
+        } else {
+            if (rf + slack(rf) + tol < P - slack(P)) side = -1;
+            else if (rf - slack(rf) - tol > Q + slack(Q)) side = 1;
+        }
+    }
+    if (side == 0) return true;
+    half_acc(viol, false, apos, side, w, acc);
+    return false;
+}
+
+// Exact breakpoint of one undecided half: its Algorithm 1 scalars go to the
+// column's shared accumulators and its entry, when inside [l, u], to the
+// column's list.  Kept out of line: it runs for a few percent of the halves.
+__device__ __noinline__ void exact_put(const Dev &d, TileCol *t, bool fp, long long ri, long long ai, double r,
+                                       double a, double m, double mo, int w)
+{
+    Acc acc{0, 0, 0, 0};
+    Half h;
+    h.type = 0;
+    if (fp) fp_half_exact(r, a, m, mo, w, t->c, acc, h);
+    else int_half_exact(ri, ai, w, t->c, acc, h);
+    flush_acc(*t, acc);
+    if (h.type != 0) {
+        const int pos = atomicAdd(&t->cnt, 1);
+        d.lists[t->lbase + pos] = SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
+    }
+}
+
+// Stream one CSC part of a non-binary tile: aligned groups of 8 nonzeros per
+// thread, row states gathered together, halves classified by products.
+template <bool FP>
+__device__ __forceinline__ void nb_part(const Dev &d, TileCol *tc, int nc, const int *s_ptr)
+{
+    const int E0 = s_ptr[0], E1 = s_ptr[nc];
+    const int g1 = (E1 + 7) >> 3;
+    for (int g = (E0 >> 3) + threadIdx.x; g < g1; g += blockDim.x) {
+        const int eb = g << 3;
+        int rows[8];
+        {
+            const int4 *rp = reinterpret_cast<const int4 *>((FP ? d.cf_row : d.ci_row) + eb);
+            const int4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+            rows[0] = r0.x; rows[1] = r0.y; rows[2] = r0.z; rows[3] = r0.w;
+            rows[4] = r1.x; rows[5] = r1.y; rows[6] = r1.z; rows[7] = r1.w;
+        }
+        double dv[8];
+        int iv[8];
+        if (FP) {
+            const double2 *vp = reinterpret_cast<const double2 *>(d.cf_val + eb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { const double2 v = __ldg(vp + k); dv[2 * k] = v.x; dv[2 * k + 1] = v.y; }
+        } else {
+            const int4 *vp = reinterpret_cast<const int4 *>(d.ci_val + eb);
+            const int4 v0 = __ldg(vp), v1 = __ldg(vp + 1);
+            iv[0] = v0.x; iv[1] = v0.y; iv[2] = v0.z; iv[3] = v0.w;
+            iv[4] = v1.x; iv[5] = v1.y; iv[6] = v1.z; iv[7] = v1.w;
+        }
+        int col = find_col(s_ptr, nc, max(eb, E0));
+        ClsCtx c = cls_of(tc[col].c);
+        Acc acc{0, 0, 0, 0};
+        constexpr int B = FP ? 4 : 8;
+#pragma unroll
+        for (int b0 = 0; b0 < 8; b0 += B) {
+            int4 st0[B], st1[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int e = eb + b0 + q;
+                if (e >= E0 && e < E1) {
+                    const int4 *pp = reinterpret_cast<const int4 *>(d.rs + rows[b0 + q]);
+                    st0[q] = __ldg(pp);
+                    if (FP) st1[q] = __ldg(pp + 1);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int e = eb + b0 + q;
+                if (e < E0 || e >= E1) continue;
+                if (s_ptr[col + 1] <= e) {
+                    while (s_ptr[col + 1] <= e) { flush_acc(tc[col], acc); ++col; }
+                    c = cls_of(tc[col].c);
+                }
+                if (FP) {
+                    const double a = dv[b0 + q];
+                    const double r = i4_double_lo(st0[q]), m1 = i4_double_lo(st1[q]), m2 = i4_double_hi(st1[q]);
+                    if (classify_fp(r, a, m1, m2, st0[q].z, c, acc)) exact_put(d, tc + col, true, 0, 0, r, a, m1, m2, st0[q].z);
+                    if (st0[q].w >= 0 && classify_fp(dflip(r), dflip(a), m2, m1, st0[q].w, c, acc))
+                        exact_put(d, tc + col, true, 0, 0, dflip(r), dflip(a), m2, m1, st0[q].w);
+                } else {
+                    const long long a = iv[b0 + q];
+                    const long long r = row_r(st0[q]);
+                    if (classify_int(r, a, st0[q].z, c, acc)) exact_put(d, tc + col, false, r, a, 0, 0, 0, 0, st0[q].z);
+                    if (st0[q].w >= 0 && classify_int(-r, -a, st0[q].w, c, acc))
+                        exact_put(d, tc + col, false, -r, -a, 0, 0, 0, 0, st0[q].w);
+                }
+            }
+        }
+        flush_acc(tc[col], acc);
+    }
+}
+
+// Candidate evaluation of one sorted entry (prefix sums P / Pc inclusive).
+__device__ __forceinline__ void eval_sorted(VCand &vb, const TileCol &t, unsigned long long kk, long long del,
+                                            unsigned aux, long long P, int Pc, unsigned long long kprev, bool has_prev,
+                                            unsigned long long knext, unsigned anext, long long nviol, long long bestnv)
+{
+    if (!is_candidate(kk, aux, kprev, has_prev, knext, anext)) return;
+    const bool post = aux_post(aux) != 0;
+    const long long Pi = P - (post ? del : 0);
+    const int Pci = Pc - (post ? aux_dc(aux) : 0);
+    const bool right = kk > t.c.kxb;
+    consider(vb, t.c, kk, t.beta + Pi + (right ? t.alpha : 0), t.beta_c + Pci + (right ? t.alpha_c : 0), nviol, bestnv);
+}
 
 template <int K>
 __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long long (&del)[K], unsigned (&aux)[K],
@@ -465,10 +971,9 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long 
                 for (int k = 0; k < K; ++k) {
                     if ((k & stride) == 0) {
                         const int k2 = k | stride;
-                        int i = lane * K + k;
-                        bool asc = (i & size) == 0;
-                        bool gt = entry_less(key[k2], aux[k2], key[k], aux[k]);
-                        if (gt == asc) {
+                        const int i = lane * K + k;
+                        const bool asc = (i & size) == 0;
+                        if (entry_less(key[k2], aux[k2], key[k], aux[k]) == asc) {
                             unsigned long long tk = key[k]; key[k] = key[k2]; key[k2] = tk;
                             long long td = del[k]; del[k] = del[k2]; del[k2] = td;
                             unsigned ta = aux[k]; aux[k] = aux[k2]; aux[k2] = ta;
@@ -482,11 +987,10 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long 
                     unsigned long long pk = __shfl_xor_sync(FULLMASK, key[k], ls);
                     long long pd = __shfl_xor_sync(FULLMASK, del[k], ls);
                     unsigned pa = __shfl_xor_sync(FULLMASK, aux[k], ls);
-                    int i = lane * K + k;
-                    bool lower = (i & stride) == 0;
-                    bool asc = (i & size) == 0;
-                    bool take = (lower == asc) ? entry_less(pk, pa, key[k], aux[k])
-                                               : entry_less(key[k], aux[k], pk, pa);
+                    const int i = lane * K + k;
+                    const bool lower = (i & stride) == 0;
+                    const bool asc = (i & size) == 0;
+                    bool take = (lower == asc) ? entry_less(pk, pa, key[k], aux[k]) : entry_less(key[k], aux[k], pk, pa);
                     if (take) { key[k] = pk; del[k] = pd; aux[k] = pa; }
                 }
             }
@@ -494,58 +998,27 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long 
     }
 }
 
-// Algorithm 1 for one column by one warp; the staged entries of this warp live
-// in skey/sdel/saux (capacity 32 * K).
+// One column per warp, K entries per lane (segments of up to 32K entries).
 template <int K>
-__device__ void nb_warp_column(const Dev &d, const VarOut &o, int j, int lane, unsigned long long *skey,
-                               long long *sdel, unsigned *saux, long long iter, long long nviol, long long bestnv,
-                               Cand &best)
+__device__ void warp_sort(const Dev &d, const VarOut &o, const TileCol &t, const SEnt *pool, long long nviol,
+                          long long bestnv, Cand &best)
 {
-    const double xb = d.x[j];
-    const bool isint = __ldg(d.vtype + j) == kVarInt;
-    const double l = __ldg(d.lb + j), u = __ldg(d.ub + j);
-    const int ci0 = __ldg(d.ci_ptr + j), nI = __ldg(d.ci_ptr + j + 1) - ci0;
-    const int cf0 = __ldg(d.cf_ptr + j), nF = __ldg(d.cf_ptr + j + 1) - cf0;
-    Acc acc{0, 0, 0, 0};
-    const bool fl = isfinite(l), fu = isfinite(u);
-    int cnt = (fl ? 1 : 0) + (fu ? 1 : 0);
-    if (lane == 0) {
-        if (fl) { skey[0] = ord_key(__dadd_rn(l, 0.0)); sdel[0] = 0; saux[0] = make_aux(0, 0); }
-        if (fu) { int p = fl ? 1 : 0; skey[p] = ord_key(__dadd_rn(u, 0.0)); sdel[p] = 0; saux[p] = make_aux(0, 0); }
-    }
-    const int total = nI + nF;
-    for (int base = 0; base < total; base += 32) {
-        int v = base + lane;
-        Half h1, h2;
-        h1.type = 0;
-        h2.type = 0;
-        if (v < total) gen_entry(d, ci0, cf0, nI, v, xb, isint, l, u, acc, h1, h2);
-        int c = half_count(h1) + half_count(h2);
-        int incl = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int t = __shfl_up_sync(FULLMASK, incl, off);
-            if (lane >= off) incl += t;
-        }
-        int pos = cnt + incl - c;
-        put_half(h1, pos, skey, sdel, saux);
-        put_half(h2, pos + half_count(h1), skey, sdel, saux);
-        cnt += __shfl_sync(FULLMASK, incl, 31);
-    }
-    __syncwarp();
-    warp_allreduce_acc(acc);
+    const int lane = threadIdx.x & 31;
     unsigned long long key[K];
     long long del[K];
     unsigned aux[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        int idx = lane * K + k;
-        if (idx < cnt) { key[k] = skey[idx]; del[k] = sdel[idx]; aux[k] = saux[idx]; }
+        const int idx = lane * K + k;
+        if (idx < t.cnt) {
+            const int4 raw = __ldcg(reinterpret_cast<const int4 *>(pool + idx));
+            key[k] = ((unsigned long long)(unsigned)raw.y << 32) | (unsigned)raw.x;
+            del[k] = raw.z;
+            aux[k] = (unsigned)raw.w;
+        }
         else { key[k] = kPadKey; del[k] = 0; aux[k] = make_aux(1, 0); }
     }
-    __syncwarp();
     warp_bitonic<K>(key, del, aux, lane);
-    // inclusive scan of the score and count deltas along the sorted entries
     long long P[K];
     int Pc[K];
     long long run = 0;
@@ -556,84 +1029,250 @@ __device__ void nb_warp_column(const Dev &d, const VarOut &o, int j, int lane, u
     int totc = runc;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
+        const long long x = __shfl_up_sync(FULLMASK, tot, off);
+        const int y = __shfl_up_sync(FULLMASK, totc, off);
+        if (lane >= off) { tot += x; totc += y; }
+    }
+    const long long ex = tot - run;
+    const int exc = totc - runc;
+    unsigned long long nk = __shfl_down_sync(FULLMASK, key[0], 1);
+    unsigned na = __shfl_down_sync(FULLMASK, aux[0], 1);
+    const unsigned long long pk = __shfl_up_sync(FULLMASK, key[K - 1], 1);
+    if (lane == 31) { nk = kPadKey; na = make_aux(1, 0); }
+    VCand vb{0, 0ull, 0, 0};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const unsigned long long knext = (k + 1 < K) ? key[(k + 1) % K] : nk;
+        const unsigned anext = (k + 1 < K) ? aux[(k + 1) % K] : na;
+        const unsigned long long kprev = (k > 0) ? key[(k + K - 1) % K] : pk;
+        eval_sorted(vb, t, key[k], del[k], aux[k], ex + P[k], exc + Pc[k], kprev, k > 0 || lane > 0, knext, anext,
+                    nviol, bestnv);
+    }
+    warp_reduce_vc(vb, t.c);
+    if (lane == 0) finish_column(d, o, t.c, vb, best);
+}
+
+// Sort, scan and argmax of one column's entries staged in shared memory, on
+// S lanes of the warp (one entry per lane, S = 8, 16 or 32).
+template <int S>
+__device__ void lane_sort(const Dev &d, const VarOut &o, const TileCol &t, const SEnt *ent, long long nviol,
+                          long long bestnv, Cand &best)
+{
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (S - 1);
+    const bool own = lane < S;
+    unsigned long long key = kPadKey;
+    long long del = 0;
+    unsigned aux = make_aux(1, 0);
+    if (own && sub < t.cnt) {
+        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(ent + sub));
+        key = ((unsigned long long)(unsigned)raw.y << 32) | (unsigned)raw.x;
+        del = raw.z;
+        aux = (unsigned)raw.w;
+    }
+#pragma unroll
+    for (int size = 2; size <= S; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const unsigned long long pk = __shfl_xor_sync(FULLMASK, key, stride);
+            const long long pd = __shfl_xor_sync(FULLMASK, del, stride);
+            const unsigned pa = __shfl_xor_sync(FULLMASK, aux, stride);
+            const bool lower = (sub & stride) == 0;
+            const bool asc = (sub & size) == 0;
+            const bool take = (lower == asc) ? entry_less(pk, pa, key, aux) : entry_less(key, aux, pk, pa);
+            if (take) { key = pk; del = pd; aux = pa; }
+        }
+    }
+    long long P = del;
+    int Pc = aux_dc(aux);
+#pragma unroll
+    for (int off = 1; off < S; off <<= 1) {
+        const long long x = __shfl_up_sync(FULLMASK, P, off, S);
+        const int y = __shfl_up_sync(FULLMASK, Pc, off, S);
+        if (sub >= off) { P += x; Pc += y; }
+    }
+    unsigned long long knext = __shfl_down_sync(FULLMASK, key, 1, S);
+    unsigned anext = __shfl_down_sync(FULLMASK, aux, 1, S);
+    const unsigned long long kprev = __shfl_up_sync(FULLMASK, key, 1, S);
+    if (sub == S - 1) { knext = kPadKey; anext = make_aux(1, 0); }
+    VCand vb{0, 0ull, 0, 0};
+    if (own) eval_sorted(vb, t, key, del, aux, P, Pc, kprev, sub > 0, knext, anext, nviol, bestnv);
+    warp_reduce_vc(vb, t.c);
+    if (lane == 0) finish_column(d, o, t.c, vb, best);
+}
+
+// Short non-binary columns (at most kWarpSortMax breakpoint entries), one
+// thread per column.  After filtering, such a column has a handful of entries
+// inside [l, u], so a sequential pass per column beats any lane-parallel
+// network: the thread walks its nonzeros (row states gathered four at a time),
+// classifies every half by products, computes the exact breakpoint of the few
+// undecided halves into the column's list (scratch), insertion-sorts the list
+// by (t, marker), scans it and keeps the best admissible entry.
+// Exact breakpoint of one undecided half: the entry (type 0: none) and the
+// Algorithm 1 scalar increments.  Out of line: a few percent of the halves
+// take it, and a single copy keeps the streaming loop small.
+struct ExactOut {
+    unsigned long long key;
+    long long D;
+    long long beta, alpha;
+    int beta_c, alpha_c;
+    int type;
+};
+
+__device__ __noinline__ ExactOut exact_half(const ColCtx *c, int fp, long long ri, long long ai, double r, double a,
+                                            double m, double mo, int w)
+{
+    Acc acc{0, 0, 0, 0};
+    Half h;
+    h.type = 0;
+    if (fp) fp_half_exact(r, a, m, mo, w, *c, acc, h);
+    else int_half_exact(ri, ai, w, *c, acc, h);
+    return ExactOut{h.key, h.D, acc.beta, acc.alpha, acc.beta_c, acc.alpha_c, h.type};
+}
+
+__device__ __forceinline__ void take_exact(const ExactOut &x, Acc &acc, SEnt *list, int &cnt)
+{
+    acc.beta += x.beta;
+    acc.alpha += x.alpha;
+    acc.beta_c += x.beta_c;
+    acc.alpha_c += x.alpha_c;
+    if (x.type != 0) list[cnt++] = SEnt{x.key, (int)x.D, x.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
+}
+
+__global__ void __launch_bounds__(kNbThreads, 6) k_eval_nb(Dev d, const Tile *tiles, VarOut o, int slot0, int gate)
+{
+    if (gated_done(d, gate)) return;
+    __shared__ ColCtx s_ctx[kNbThreads];
+    const Tile tl = tiles[blockIdx.x];
+    const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
+    Cand best{0, kNoVar, 0, 0.0};
+    const int q = tl.begin + threadIdx.x;
+    if (q < tl.end) {
+        ColCtx &c = s_ctx[threadIdx.x];
+        c = make_col(d, q, iter);
+        const ClsCtx k = cls_of(c);
+        SEnt *list = d.lists + __ldg(d.list_off + (q - d.nb_pos0));
+        int cnt = 0;
+        const double l = __ldg(d.lb + c.j), u = __ldg(d.ub + c.j);
+        if (isfinite(l)) list[cnt++] = SEnt{c.kl, 0, make_aux(0, 0)};
+        if (isfinite(u)) list[cnt++] = SEnt{c.ku, 0, make_aux(0, 0)};
+        Acc acc{0, 0, 0, 0};
+        for (int v0 = 0; v0 < c.nI; v0 += 4) {
+            int rows[4], av[4];
+            int4 st[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (v0 + t < c.nI) { rows[t] = __ldg(d.ci_row + c.ci0 + v0 + t); av[t] = __ldg(d.ci_val + c.ci0 + v0 + t); }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (v0 + t < c.nI) st[t] = ld_row16(d.rs + rows[t]);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (v0 + t >= c.nI) break;
+                const long long r = row_r(st[t]), a = av[t];
+                if (classify_int(r, a, st[t].z, k, acc))
+                    take_exact(exact_half(&c, 0, r, a, 0.0, 0.0, 0.0, 0.0, st[t].z), acc, list, cnt);
+                if (st[t].w >= 0 && classify_int(-r, -a, st[t].w, k, acc))
+                    take_exact(exact_half(&c, 0, -r, -a, 0.0, 0.0, 0.0, 0.0, st[t].w), acc, list, cnt);
+            }
+        }
+        for (int v0 = 0; v0 < c.nF; v0 += 4) {
+            int rows[4];
+            double av[4];
+            int4 s0[4], s1[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (v0 + t < c.nF) { rows[t] = __ldg(d.cf_row + c.cf0 + v0 + t); av[t] = __ldg(d.cf_val + c.cf0 + v0 + t); }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (v0 + t < c.nF) {
+                    const int4 *p = reinterpret_cast<const int4 *>(d.rs + rows[t]);
+                    s0[t] = __ldg(p);
+                    s1[t] = __ldg(p + 1);
+                }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (v0 + t >= c.nF) break;
+                const double a = av[t];
+                const double r = i4_double_lo(s0[t]), m1 = i4_double_lo(s1[t]), m2 = i4_double_hi(s1[t]);
+                if (classify_fp(r, a, m1, m2, s0[t].z, k, acc))
+                    take_exact(exact_half(&c, 1, 0, 0, r, a, m1, m2, s0[t].z), acc, list, cnt);
+                if (s0[t].w >= 0 && classify_fp(dflip(r), dflip(a), m2, m1, s0[t].w, k, acc))
+                    take_exact(exact_half(&c, 1, 0, 0, dflip(r), dflip(a), m2, m1, s0[t].w), acc, list, cnt);
+            }
+        }
+        // insertion sort by (t, marker)
+        for (int i = 1; i < cnt; ++i) {
+            const SEnt e = list[i];
+            int j = i - 1;
+            while (j >= 0 && entry_less(e.key, e.aux, list[j].key, list[j].aux)) { list[j + 1] = list[j]; --j; }
+            list[j + 1] = e;
+        }
+        // scan and argmax (Algorithm 1, phases 3-4)
+        long long P = 0;
+        int Pc = 0;
+        VCand vb{0, 0ull, 0, 0};
+        unsigned long long kprev = 0ull;
+        for (int i = 0; i < cnt; ++i) {
+            const SEnt e = list[i];
+            P += e.del;
+            Pc += aux_dc(e.aux);
+            const unsigned long long knext = i + 1 < cnt ? list[i + 1].key : kPadKey;
+            const unsigned anext = i + 1 < cnt ? list[i + 1].aux : make_aux(1, 0);
+            if (is_candidate(e.key, e.aux, kprev, i > 0, knext, anext)) {
+                const bool post = aux_post(e.aux) != 0;
+                const long long Pi = P - (post ? e.del : 0);
+                const int Pci = Pc - (post ? aux_dc(e.aux) : 0);
+                const bool right = e.key > c.kxb;
+                consider(vb, c, e.key, acc.beta + Pi + (right ? acc.alpha : 0),
+                         acc.beta_c + Pci + (right ? acc.alpha_c : 0), nviol, bestnv);
+            }
+            kprev = e.key;
+        }
+        finish_column(d, o, c, vb, best);
+    }
+    const Cand bb = block_reduce_cand(best);
+    if (threadIdx.x == 0) d.block_best[slot0 + blockIdx.x] = bb;
+}
+
+// ------------------------------------------------- CTA bitonic sort (smem)
+
+__device__ __forceinline__ void block_scan2(long long &v, int &vc, long long *wsum, int *wsumc)
+{
+    // exclusive block scan of (v, vc); returns the exclusive prefix in (v, vc)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long tot = v;
+    int totc = vc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
         long long a = __shfl_up_sync(FULLMASK, tot, off);
         int b = __shfl_up_sync(FULLMASK, totc, off);
         if (lane >= off) { tot += a; totc += b; }
     }
-    long long ex = tot - run;
-    int exc = totc - runc;
-    unsigned long long nk = __shfl_down_sync(FULLMASK, key[0], 1);
-    unsigned na = __shfl_down_sync(FULLMASK, aux[0], 1);
-    if (lane == 31) { nk = kPadKey; na = make_aux(1, 0); }
-    VCand vb{0, 0.0, 0, 0};
+    if (lane == 31) { wsum[warp] = tot; wsumc[warp] = totc; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        long long x = lane < nw ? wsum[lane] : 0;
+        int xc = lane < nw ? wsumc[lane] : 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        unsigned long long kk = key[k];
-        unsigned long long nxk = (k + 1 < K) ? key[(k + 1) % K] : nk;
-        unsigned nxa = (k + 1 < K) ? aux[(k + 1) % K] : na;
-        bool cand = kk != kPadKey && aux_plus(aux[k]) == 0 && (nxk != kk || aux_plus(nxa) != 0);
-        if (!cand) continue;
-        double t = key_to_double(kk);
-        if (t == xb) continue;
-        bool right = t > xb;
-        long long sg = acc.beta + ex + P[k] + (right ? acc.alpha : 0);
-        int dcv = acc.beta_c + exc + Pc[k] + (right ? acc.alpha_c : 0);
-        if (!admissible(right, j, dcv, d, iter, nviol, bestnv)) continue;
-        VCand c{sg, t, dcv, 1};
-        if (vc_better(c, vb, xb)) vb = c;
+        for (int off = 1; off < 32; off <<= 1) {
+            long long a = __shfl_up_sync(FULLMASK, x, off);
+            int b = __shfl_up_sync(FULLMASK, xc, off);
+            if (lane >= off) { x += a; xc += b; }
+        }
+        if (lane < nw) { wsum[lane] = x; wsumc[lane] = xc; }
     }
-    warp_reduce_vc(vb, xb);
-    if (lane == 0) finish_column(d, o, j, xb, vb, best);
-    __syncwarp();
-}
-
-template <int K>
-__device__ void eval_nb_tile(const Dev &d, const Tile &tl, const VarOut &o, long long iter, long long nviol,
-                             long long bestnv, Cand &best, unsigned long long *skey, long long *sdel,
-                             unsigned *saux)
-{
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = tl.begin + warp; q < tl.end; q += kEvalThreads / 32) {
-        int j = __ldg(d.var_list + q);
-        nb_warp_column<K>(d, o, j, lane, skey, sdel, saux, iter, nviol, bestnv, best);
-    }
-}
-
-// ------------------------------------------------------------ eval kernels
-
-__device__ __forceinline__ bool gated_done(const Dev &d, int gate)
-{
-    return gate && *(volatile int *)&d.ctl->done;
-}
-
-__global__ void __launch_bounds__(kEvalThreads) k_eval_small(Dev d, const Tile *tiles, VarOut o, int gate)
-{
-    if (gated_done(d, gate)) return;
-    __shared__ unsigned long long skey[kEvalThreads / 32][kWarpStageCap];
-    __shared__ long long sdel[kEvalThreads / 32][kWarpStageCap];
-    __shared__ unsigned saux[kEvalThreads / 32][kWarpStageCap];
-    const Tile tl = tiles[blockIdx.x];
-    const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
-    Cand best{0, kNoVar, 0, 0.0};
-    int warp = threadIdx.x >> 5;
-    switch (tl.kind) {
-    case T_BIN_G4: eval_bin_tile<4>(d, tl, o, iter, nviol, bestnv, best); break;
-    case T_BIN_G8: eval_bin_tile<8>(d, tl, o, iter, nviol, bestnv, best); break;
-    case T_BIN_G16: eval_bin_tile<16>(d, tl, o, iter, nviol, bestnv, best); break;
-    case T_BIN_G32: eval_bin_tile<32>(d, tl, o, iter, nviol, bestnv, best); break;
-    case T_BIN_CTA: eval_bin_cta(d, tl, o, iter, nviol, bestnv, best); break;
-    case T_NB_K1: eval_nb_tile<1>(d, tl, o, iter, nviol, bestnv, best, skey[warp], sdel[warp], saux[warp]); break;
-    case T_NB_K2: eval_nb_tile<2>(d, tl, o, iter, nviol, bestnv, best, skey[warp], sdel[warp], saux[warp]); break;
-    case T_NB_K4: eval_nb_tile<4>(d, tl, o, iter, nviol, bestnv, best, skey[warp], sdel[warp], saux[warp]); break;
-    case T_NB_K8: eval_nb_tile<8>(d, tl, o, iter, nviol, bestnv, best, skey[warp], sdel[warp], saux[warp]); break;
-    default: break;
-    }
-    Cand b = block_reduce_cand(best);
-    if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
+    __syncthreads();
+    long long ex = (tot - v) + (warp > 0 ? wsum[warp - 1] : 0);
+    int exc = (totc - vc) + (warp > 0 ? wsumc[warp - 1] : 0);
+    v = ex;
+    vc = exc;
+    __syncthreads();
 }
 
 // One column per CTA, entries sorted in shared memory (bitonic, N = tile.aux).
-__global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *tiles, VarOut o, int slot_base, int gate)
+__global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *tiles, VarOut o, int slot0, int gate)
 {
     if (gated_done(d, gate)) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -645,31 +1284,29 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
     __shared__ int s_cnt;
     __shared__ long long s_beta, s_alpha;
     __shared__ int s_bc, s_ac;
+    __shared__ long long wsum[32];
+    __shared__ int wsumc[32];
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
-    const int j = __ldg(d.var_list + tl.begin);
-    const double xb = d.x[j];
-    const bool isint = __ldg(d.vtype + j) == kVarInt;
-    const double l = __ldg(d.lb + j), u = __ldg(d.ub + j);
-    const int ci0 = __ldg(d.ci_ptr + j), nI = __ldg(d.ci_ptr + j + 1) - ci0;
-    const int cf0 = __ldg(d.cf_ptr + j), nF = __ldg(d.cf_ptr + j + 1) - cf0;
+    const ColCtx c = make_col(d, tl.begin, iter);
+    const double l = __ldg(d.lb + c.j), u = __ldg(d.ub + c.j);
     const bool fl = isfinite(l), fu = isfinite(u);
     if (threadIdx.x == 0) {
         s_cnt = (fl ? 1 : 0) + (fu ? 1 : 0);
         s_beta = 0; s_alpha = 0; s_bc = 0; s_ac = 0;
-        if (fl) { skey[0] = ord_key(__dadd_rn(l, 0.0)); sdel[0] = 0; saux[0] = make_aux(0, 0); }
-        if (fu) { int p = fl ? 1 : 0; skey[p] = ord_key(__dadd_rn(u, 0.0)); sdel[p] = 0; saux[p] = make_aux(0, 0); }
+        if (fl) { skey[0] = c.kl; sdel[0] = 0; saux[0] = make_aux(0, 0); }
+        if (fu) { int p = fl ? 1 : 0; skey[p] = c.ku; sdel[p] = 0; saux[p] = make_aux(0, 0); }
     }
     __syncthreads();
     Acc acc{0, 0, 0, 0};
-    const int total = nI + nF;
+    const int total = c.nI + c.nF;
     for (int v = threadIdx.x; v < total; v += blockDim.x) {
         Half h1, h2;
-        gen_entry(d, ci0, cf0, nI, v, xb, isint, l, u, acc, h1, h2);
-        int c = half_count(h1) + half_count(h2);
-        if (c) {
-            int pos = atomicAdd(&s_cnt, c);
-            put_half(h1, pos, skey, sdel, saux);
-            put_half(h2, pos + half_count(h1), skey, sdel, saux);
+        gen_entry(d, c, v, acc, h1, h2);
+        const int n1 = h1.type != 0, n2 = h2.type != 0;
+        if (n1 + n2) {
+            int pos = atomicAdd(&s_cnt, n1 + n2);
+            if (n1) put_half(h1, pos, skey, sdel, saux);
+            if (n2) put_half(h2, pos + n1, skey, sdel, saux);
         }
     }
     warp_allreduce_acc(acc);
@@ -683,17 +1320,15 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
     const int cnt = s_cnt;
     for (int i = cnt + threadIdx.x; i < N; i += blockDim.x) { skey[i] = kPadKey; sdel[i] = 0; saux[i] = make_aux(1, 0); }
     __syncthreads();
-    // bitonic sort of N entries in shared memory
     for (int size = 2; size <= N; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
-                int i = 2 * stride * (p / stride) + (p % stride);
-                int k2 = i + stride;
-                bool asc = (i & size) == 0;
+                const int i = 2 * stride * (p / stride) + (p % stride);
+                const int k2 = i + stride;
+                const bool asc = (i & size) == 0;
                 unsigned long long ka = skey[i], kb = skey[k2];
                 unsigned aa = saux[i], ab = saux[k2];
-                bool gt = entry_less(kb, ab, ka, aa);
-                if (gt == asc) {
+                if (entry_less(kb, ab, ka, aa) == asc) {
                     skey[i] = kb; skey[k2] = ka;
                     saux[i] = ab; saux[k2] = aa;
                     long long t = sdel[i]; sdel[i] = sdel[k2]; sdel[k2] = t;
@@ -702,115 +1337,79 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
             __syncthreads();
         }
     }
-    // block scan: each thread owns N / blockDim consecutive entries
     const int per = N / blockDim.x;
     const int b0 = threadIdx.x * per;
     long long run = 0;
     int runc = 0;
     for (int q = 0; q < per; ++q) { run += sdel[b0 + q]; runc += aux_dc(saux[b0 + q]); }
-    __shared__ long long wsum[32];
-    __shared__ int wsumc[32];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long tot = run;
-    int totc = runc;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        long long a = __shfl_up_sync(FULLMASK, tot, off);
-        int b = __shfl_up_sync(FULLMASK, totc, off);
-        if (lane >= off) { tot += a; totc += b; }
-    }
-    if (lane == 31) { wsum[warp] = tot; wsumc[warp] = totc; }
-    __syncthreads();
-    if (warp == 0) {
-        int nw = blockDim.x >> 5;
-        long long v = lane < nw ? wsum[lane] : 0;
-        int vc = lane < nw ? wsumc[lane] : 0;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            long long a = __shfl_up_sync(FULLMASK, v, off);
-            int b = __shfl_up_sync(FULLMASK, vc, off);
-            if (lane >= off) { v += a; vc += b; }
-        }
-        if (lane < nw) { wsum[lane] = v; wsumc[lane] = vc; }
-    }
-    __syncthreads();
-    long long ex = (tot - run) + (warp > 0 ? wsum[warp - 1] : 0);
-    int exc = (totc - runc) + (warp > 0 ? wsumc[warp - 1] : 0);
+    long long P = run;
+    int Pc = runc;
+    block_scan2(P, Pc, wsum, wsumc);
     const long long beta = s_beta, alpha = s_alpha;
     const int bc = s_bc, ac = s_ac;
-    VCand vb{0, 0.0, 0, 0};
-    long long P = ex;
-    int Pc = exc;
+    VCand vb{0, 0ull, 0, 0};
     for (int q = 0; q < per; ++q) {
-        int i = b0 + q;
-        unsigned long long kk = skey[i];
-        unsigned a = saux[i];
+        const int i = b0 + q;
+        const unsigned long long kk = skey[i];
+        const unsigned a = saux[i];
         P += sdel[i];
         Pc += aux_dc(a);
-        if (kk == kPadKey || aux_plus(a) != 0) continue;
-        bool last = (i + 1 >= N) || skey[i + 1] != kk || aux_plus(saux[i + 1]) != 0;
-        if (!last) continue;
-        double t = key_to_double(kk);
-        if (t == xb) continue;
-        bool right = t > xb;
-        long long sg = beta + P + (right ? alpha : 0);
-        int dcv = bc + Pc + (right ? ac : 0);
-        if (!admissible(right, j, dcv, d, iter, nviol, bestnv)) continue;
-        VCand c{sg, t, dcv, 1};
-        if (vc_better(c, vb, xb)) vb = c;
+        const unsigned long long knext = i + 1 < N ? skey[i + 1] : kPadKey;
+        const unsigned anext = i + 1 < N ? saux[i + 1] : make_aux(1, 0);
+        const unsigned long long kprev = i > 0 ? skey[i - 1] : 0ull;
+        if (!is_candidate(kk, a, kprev, i > 0, knext, anext)) continue;
+        const bool post = aux_post(a) != 0;
+        const long long Pi = P - (post ? sdel[i] : 0);
+        const int Pci = Pc - (post ? aux_dc(a) : 0);
+        const bool right = kk > c.kxb;
+        consider(vb, c, kk, beta + Pi + (right ? alpha : 0), bc + Pci + (right ? ac : 0), nviol, bestnv);
     }
-    vb = block_reduce_vc(vb, xb);
+    vb = block_reduce_vc(vb, c);
     if (threadIdx.x == 0) {
         Cand best{0, kNoVar, 0, 0.0};
-        finish_column(d, o, j, xb, vb, best);
-        d.block_best[slot_base + blockIdx.x] = best;
+        finish_column(d, o, c, vb, best);
+        d.block_best[slot0 + blockIdx.x] = best;
     }
 }
 
-// Long integer column with a small domain: every CTA bins one chunk of the
-// column's nonzeros by breakpoint value (a counting sort on the key (t,
-// marker)); the last CTA of the column scans the bins and takes the argmax.
+// ------------------------------- multi-CTA counting sort (long integer columns)
+
+// Every CTA bins one chunk of the column's nonzeros by breakpoint value; the
+// last CTA of the column scans the bins in value order and takes the argmax.
 __global__ void __launch_bounds__(kHistThreads) k_eval_hist(Dev d, const Tile *tiles, VarOut o, int gate)
 {
     if (gated_done(d, gate)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     HBin *sb = reinterpret_cast<HBin *>(smem);
+    __shared__ long long wsum[32];
+    __shared__ int wsumc[32];
+    __shared__ int s_last;
     const Tile tl = tiles[blockIdx.x];
     const HistCol hc = d.hcols[tl.begin];
     const int chunk = tl.aux;
-    const int j = hc.var;
-    const double xb = d.x[j];
-    const double l = __ldg(d.lb + j), u = __ldg(d.ub + j);
-    const int D = (int)(u - l) + 1;
-    const int ci0 = __ldg(d.ci_ptr + j), nI = __ldg(d.ci_ptr + j + 1) - ci0;
-    const int cf0 = __ldg(d.cf_ptr + j);
-    const int total = hc.e_end;
-    for (int b = threadIdx.x; b < D; b += blockDim.x) sb[b] = HBin{0, 0, 0, 0, 0, 0};
+    const ColCtx c = make_col(d, hc.pos, d.ctl->iter);
+    const long long lo = ikey_val(c.kl);
+    const int D = (int)(ikey_val(c.ku) - lo) + 1;
+    for (int b = threadIdx.x; b < D; b += blockDim.x) sb[b] = HBin{0, 0, 0, 0};
     __syncthreads();
     const int v0 = chunk * kHistChunk;
-    const int v1 = min(total, v0 + kHistChunk);
+    const int v1 = min(hc.e_end, v0 + kHistChunk);
     Acc acc{0, 0, 0, 0};
     for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
         Half h[2];
-        gen_entry(d, ci0, cf0, nI, v, xb, true, l, u, acc, h[0], h[1]);
+        gen_entry(d, c, v, acc, h[0], h[1]);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             if (h[q].type == 0) continue;
-            int b = (int)(h[q].t - l);
-            HBin *p = sb + b;
-            atomicAdd(&p->np, 1);
+            HBin *p = sb + (int)(ikey_val(h[q].key) - lo);
             if (h[q].type == 1) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&p->sm), (unsigned long long)h[q].D);
-                atomicAdd(&p->cm, -1);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&p->spre), (unsigned long long)h[q].D);
+                atomicAdd(&p->n1, 1);
             } else {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&p->sp), (unsigned long long)h[q].D);
-                atomicAdd(&p->cp, 1);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&p->spost), (unsigned long long)h[q].D);
+                atomicAdd(&p->n2, 1);
             }
         }
-    }
-    if (chunk == 0 && threadIdx.x == 0) {
-        atomicAdd(&sb[0].np, 1);      // bound entry (l, -1, 0)
-        atomicAdd(&sb[D - 1].np, 1);  // bound entry (u, -1, 0)
     }
     warp_allreduce_acc(acc);
     HistAcc *ha = d.hacc + tl.begin;
@@ -823,23 +1422,18 @@ __global__ void __launch_bounds__(kHistThreads) k_eval_hist(Dev d, const Tile *t
     __syncthreads();
     HBin *gb = d.hbins + hc.bin_off;
     for (int b = threadIdx.x; b < D; b += blockDim.x) {
-        HBin s = sb[b];
-        if (s.np | s.cm | s.cp) {
-            if (s.sm) atomicAdd(reinterpret_cast<unsigned long long *>(&gb[b].sm), (unsigned long long)s.sm);
-            if (s.sp) atomicAdd(reinterpret_cast<unsigned long long *>(&gb[b].sp), (unsigned long long)s.sp);
-            if (s.cm) atomicAdd(&gb[b].cm, s.cm);
-            if (s.cp) atomicAdd(&gb[b].cp, s.cp);
-            if (s.np) atomicAdd(&gb[b].np, s.np);
-        }
+        const HBin s = sb[b];
+        if (s.spre) atomicAdd(reinterpret_cast<unsigned long long *>(&gb[b].spre), (unsigned long long)s.spre);
+        if (s.spost) atomicAdd(reinterpret_cast<unsigned long long *>(&gb[b].spost), (unsigned long long)s.spost);
+        if (s.n1) atomicAdd(&gb[b].n1, s.n1);
+        if (s.n2) atomicAdd(&gb[b].n2, s.n2);
     }
     __threadfence();
     __syncthreads();
-    __shared__ int s_last;
     if (threadIdx.x == 0) s_last = (atomicAdd(&ha->ticket, 1u) == (unsigned)(hc.nchunks - 1));
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // last CTA of the column: scan the bins in value order
     const long long beta = __ldcg(&ha->beta), alpha = __ldcg(&ha->alpha);
     const int bc = __ldcg(&ha->beta_c), ac = __ldcg(&ha->alpha_c);
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
@@ -848,72 +1442,39 @@ __global__ void __launch_bounds__(kHistThreads) k_eval_hist(Dev d, const Tile *t
     long long run = 0;
     int runc = 0;
     for (int q = 0; q < per; ++q) {
-        int b = b0 + q;
+        const int b = b0 + q;
         if (b >= D) break;
-        run += __ldcg(&gb[b].sm) + __ldcg(&gb[b].sp);
-        runc += __ldcg(&gb[b].cm) + __ldcg(&gb[b].cp);
+        run += __ldcg(&gb[b].spre) + __ldcg(&gb[b].spost);
+        runc += __ldcg(&gb[b].n2) - __ldcg(&gb[b].n1);
     }
-    __shared__ long long wsum[32];
-    __shared__ int wsumc[32];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long tot = run;
-    int totc = runc;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        long long a = __shfl_up_sync(FULLMASK, tot, off);
-        int b = __shfl_up_sync(FULLMASK, totc, off);
-        if (lane >= off) { tot += a; totc += b; }
-    }
-    if (lane == 31) { wsum[warp] = tot; wsumc[warp] = totc; }
-    __syncthreads();
-    if (warp == 0) {
-        int nw = blockDim.x >> 5;
-        long long v = lane < nw ? wsum[lane] : 0;
-        int vc = lane < nw ? wsumc[lane] : 0;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            long long a = __shfl_up_sync(FULLMASK, v, off);
-            int b = __shfl_up_sync(FULLMASK, vc, off);
-            if (lane >= off) { v += a; vc += b; }
-        }
-        if (lane < nw) { wsum[lane] = v; wsumc[lane] = vc; }
-    }
-    __syncthreads();
-    long long P = (tot - run) + (warp > 0 ? wsum[warp - 1] : 0);
-    int Pc = (totc - runc) + (warp > 0 ? wsumc[warp - 1] : 0);
-    VCand vb{0, 0.0, 0, 0};
+    long long P = run;
+    int Pc = runc;
+    block_scan2(P, Pc, wsum, wsumc);
+    VCand vb{0, 0ull, 0, 0};
     for (int q = 0; q < per; ++q) {
-        int b = b0 + q;
+        const int b = b0 + q;
         if (b >= D) break;
-        HBin s;
-        s.sm = __ldcg(&gb[b].sm); s.sp = __ldcg(&gb[b].sp);
-        s.cm = __ldcg(&gb[b].cm); s.cp = __ldcg(&gb[b].cp); s.np = __ldcg(&gb[b].np);
-        long long sig_part = P + s.sm;
-        int dc_part = Pc + s.cm;
-        P += s.sm + s.sp;
-        Pc += s.cm + s.cp;
-        if (s.np == 0) continue;
-        double t = l + (double)b;
-        if (t == xb) continue;
-        bool right = t > xb;
-        long long sg = beta + sig_part + (right ? alpha : 0);
-        int dcv = bc + dc_part + (right ? ac : 0);
-        if (!admissible(right, j, dcv, d, iter, nviol, bestnv)) continue;
-        VCand c{sg, t, dcv, 1};
-        if (vc_better(c, vb, xb)) vb = c;
+        const long long spre = __ldcg(&gb[b].spre), spost = __ldcg(&gb[b].spost);
+        const int n1 = __ldcg(&gb[b].n1), n2 = __ldcg(&gb[b].n2);
+        if ((n1 | n2) != 0 || b == 0 || b == D - 1) {
+            const unsigned long long k = ikey(lo + b);
+            const bool right = k > c.kxb;
+            consider(vb, c, k, beta + P + spre + (right ? alpha : 0), bc + Pc - n1 + (right ? ac : 0), nviol, bestnv);
+        }
+        P += spre + spost;
+        Pc += n2 - n1;
     }
-    vb = block_reduce_vc(vb, xb);
-    // reset the column's scratch for the next pass
-    for (int b = threadIdx.x; b < D; b += blockDim.x) gb[b] = HBin{0, 0, 0, 0, 0, 0};
+    vb = block_reduce_vc(vb, c);
+    for (int b = threadIdx.x; b < D; b += blockDim.x) gb[b] = HBin{0, 0, 0, 0};
     if (threadIdx.x == 0) {
         Cand best{0, kNoVar, 0, 0.0};
-        finish_column(d, o, j, xb, vb, best);
+        finish_column(d, o, c, vb, best);
         d.block_best[hc.slot] = best;
         *ha = HistAcc{0, 0, 0, 0, 0u, 0};
     }
 }
 
-// Fixed variables and the default of every per-variable output.
+// Default of every per-variable output (fixed variables keep it).
 __global__ void k_fill_outputs(Dev d, VarOut o)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
@@ -975,46 +1536,43 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Dev d, int gate)
     if (var >= 0) {
         const double dl = __dsub_rn(c->mv_new, c->mv_old);
         const long long di = (long long)dl;
-        int e0 = d.ci_ptr[var], e1 = d.ci_ptr[var + 1];
+        const int q = d.vpos[var];
+        const int e0 = d.ci_ptr[q], e1 = d.ci_ptr[q + 1];
         for (int e = e0 + gtid; e < e1; e += gstride) {
-            int i = d.ci_row[e];
-            long long a = d.ci_val[e];
+            const int i = d.ci_row[e];
+            const long long a = d.ci_val[e];
             RowState *p = d.rs + i;
-            long long r0 = p->r;
-            long long r1 = r0 + a * di;
+            const long long r0 = p->r;
+            const long long r1 = r0 + a * di;
             p->r = r1;
             local += (long long)(r1 > 0) - (long long)(r0 > 0);
             if (p->w2 >= 0) local += (long long)(-r1 > 0) - (long long)(-r0 > 0);
         }
-        int f0 = d.cf_ptr[var], f1 = d.cf_ptr[var + 1];
+        const int f0 = d.cf_ptr[q], f1 = d.cf_ptr[q + 1];
         for (int e = f0 + gtid; e < f1; e += gstride) {
-            int i = d.cf_row[e];
-            double a = d.cf_val[e];
+            const int i = d.cf_row[e];
+            const double a = d.cf_val[e];
             RowState *p = d.rs + i;
-            double eps = d.eps[i];
-            double r0 = __longlong_as_double(p->r);
-            double r1 = __dadd_rn(r0, __dmul_rn(a, dl));
+            const double eps = d.eps[i];
+            const double r1 = __dadd_rn(__longlong_as_double(p->r), __dmul_rn(a, dl));
+            const double m1 = __dsub_rn(eps, r1), m2 = __dadd_rn(eps, r1);
+            local += (long long)dneg(m1) - (long long)dneg(p->m1);
+            if (p->w2 >= 0) local += (long long)dneg(m2) - (long long)dneg(p->m2);
             p->r = __double_as_longlong(r1);
-            local += (long long)(r1 > eps) - (long long)(r0 > eps);
-            if (p->w2 >= 0) local += (long long)(-r1 > eps) - (long long)(-r0 > eps);
+            p->m1 = m1;
+            p->m2 = m2;
         }
     } else {
         for (int i = gtid; i < d.m; i += gstride) {
             RowState *p = d.rs + i;
-            RowState s = *p;
+            const RowState s = *p;
             bool v1, v2;
             if (d.row_int[i]) { v1 = s.r > 0; v2 = -s.r > 0; }
-            else {
-                double r = __longlong_as_double(s.r);
-                double eps = d.eps[i];
-                v1 = r > eps;
-                v2 = -r > eps;
-            }
+            else { v1 = dneg(s.m1); v2 = dneg(s.m2); }
             if (v1) p->w1 = s.w1 + 1;
             if (s.w2 >= 0 && v2) p->w2 = s.w2 + 1;
         }
     }
-    // block reduce of the violation-count change
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULLMASK, local, off);
     __shared__ long long red[kApplyThreads / 32];
@@ -1032,14 +1590,14 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Dev d, int gate)
     if (!s_last || threadIdx.x != 0) return;
     __threadfence();
     // last CTA: finish the iteration
-    long long nv = c->nviol + (long long)__ldcg(reinterpret_cast<const long long *>(&c->nviol_delta));
+    const long long nv = c->nviol + (long long)__ldcg(reinterpret_cast<const long long *>(&c->nviol_delta));
     c->nviol = nv;
     c->nviol_delta = 0;
     c->apply_ticket = 0;
     const long long it = c->iter;
     if (var >= 0) {
         d.x[var] = c->mv_new;
-        int stamp = (int)(it + 1 + d.tenure);
+        const int stamp = (int)(it + 1 + d.tenure);
         if (c->mv_new > c->mv_old) d.tabu_dec[var] = stamp;
         else d.tabu_inc[var] = stamp;
         c->moves += 1;
@@ -1057,32 +1615,56 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Dev d, int gate)
 
 // --------------------------------------------------------- state handling
 
-// r = (sum of a x in CSR order) - b per physical row; exact int64 on integral rows.
+// r = (sum of a x in CSR order) - b per physical row, one warp per row:
+// products are formed in parallel; integral rows sum them in int64 (exact, any
+// order), the others add them in CSR order so the residual is the same double
+// as a sequential evaluation.  Also sets the margins eps -+ r and counts the
+// violated normalised rows.
 __global__ void k_residuals(Dev d)
 {
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     long long local = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += gridDim.x * blockDim.x) {
-        long long p0 = d.row_ptr[i], p1 = d.row_ptr[i + 1];
+    for (int i = wid; i < d.m; i += nw) {
+        const long long p0 = d.row_ptr[i], p1 = d.row_ptr[i + 1];
         RowState *p = d.rs + i;
         if (d.row_int[i]) {
             long long y = 0;
-            for (long long e = p0; e < p1; ++e) y += (long long)d.row_val[e] * (long long)d.x[d.col_idx[e]];
-            long long r = y - (long long)d.rhs[i];
-            p->r = r;
-            local += (r > 0) + (p->w2 >= 0 && -r > 0);
+            for (long long e = p0 + lane; e < p1; e += 32) y += (long long)d.row_val[e] * (long long)d.x[d.col_idx[e]];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(FULLMASK, y, off);
+            if (lane == 0) {
+                const long long r = y - (long long)d.rhs[i];
+                p->r = r;
+                p->m1 = 0.0;
+                p->m2 = 0.0;
+                local += (r > 0) + (p->w2 >= 0 && -r > 0);
+            }
         } else {
             double y = 0.0;
-            for (long long e = p0; e < p1; ++e) y = __dadd_rn(y, __dmul_rn(d.row_val[e], d.x[d.col_idx[e]]));
-            double r = __dsub_rn(y, d.rhs[i]);
-            p->r = __double_as_longlong(r);
-            double eps = d.eps[i];
-            local += (r > eps) + (p->w2 >= 0 && -r > eps);
+            for (long long e0 = p0; e0 < p1; e0 += 32) {
+                const long long e = e0 + lane;
+                const double t = e < p1 ? __dmul_rn(d.row_val[e], d.x[d.col_idx[e]]) : 0.0;
+                const int cnt = (int)min(32LL, p1 - e0);
+                for (int k = 0; k < cnt; ++k) {
+                    const double tk = __shfl_sync(FULLMASK, t, k);
+                    y = __dadd_rn(y, tk);
+                }
+            }
+            if (lane == 0) {
+                const double r = __dsub_rn(y, d.rhs[i]);
+                const double eps = d.eps[i];
+                p->r = __double_as_longlong(r);
+                p->m1 = __dsub_rn(eps, r);
+                p->m2 = __dadd_rn(eps, r);
+                local += dneg(p->m1) + (p->w2 >= 0 && dneg(p->m2));
+            }
         }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULLMASK, local, off);
-    if ((threadIdx.x & 31) == 0 && local)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&d.ctl->nviol), (unsigned long long)local);
+    if (lane == 0 && local) atomicAdd(reinterpret_cast<unsigned long long *>(&d.ctl->nviol), (unsigned long long)local);
 }
 
 __global__ void k_finish_set_state(Dev d, long long iter, long long best_nviol, int use_best)
@@ -1112,20 +1694,11 @@ __global__ void k_begin_run(Dev d, long long max_iters, int stop_at_feasible)
     c->done = ((stop_at_feasible && c->nviol == 0) || max_iters <= 0) ? 1 : 0;
 }
 
-__global__ void k_pack_w(Dev d, const int *w)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += gridDim.x * blockDim.x) {
-        int k = d.nrow_base[i];
-        d.rs[i].w1 = w[k];
-        if (d.rs[i].w2 >= 0) d.rs[i].w2 = w[k + 1];
-    }
-}
-
 __global__ void k_unpack_w(Dev d, int *w)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += gridDim.x * blockDim.x) {
-        int k = d.nrow_base[i];
-        RowState s = d.rs[i];
+        const int k = d.nrow_base[i];
+        const RowState s = d.rs[i];
         w[k] = s.w1;
         if (s.w2 >= 0) w[k + 1] = s.w2;
     }
@@ -1134,9 +1707,9 @@ __global__ void k_unpack_w(Dev d, int *w)
 __global__ void k_unpack_r(Dev d, double *r)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += gridDim.x * blockDim.x) {
-        int k = d.nrow_base[i];
-        RowState s = d.rs[i];
-        double v = d.row_int[i] ? (double)s.r : __longlong_as_double(s.r);
+        const int k = d.nrow_base[i];
+        const RowState s = d.rs[i];
+        const double v = d.row_int[i] ? (double)s.r : __longlong_as_double(s.r);
         r[k] = v;
         if (s.w2 >= 0) r[k + 1] = -v;
     }
@@ -1145,11 +1718,6 @@ __global__ void k_unpack_r(Dev d, double *r)
 __global__ void k_widen(int n, const int *a, long long *b)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) b[j] = a[j];
-}
-
-__global__ void k_narrow(int n, const long long *a, int *b)
-{
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) b[j] = (int)a[j];
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1162,28 +1730,39 @@ static int grid_for(long long n, int threads, int cap = 152 * 8)
     return (int)g;
 }
 
-cudaError_t setup_kernel_attributes(int cta_smem, int hist_smem)
+cudaError_t setup_kernel_attributes(const LaunchPlan &p)
 {
     cudaError_t e = cudaSuccess;
-    if (cta_smem > 0)
-        e = cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, cta_smem);
-    if (e == cudaSuccess && hist_smem > 0)
-        e = cudaFuncSetAttribute(k_eval_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, hist_smem);
+    if (p.nb_smem > 0) e = cudaFuncSetAttribute(k_eval_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, p.nb_smem);
+    if (e == cudaSuccess && p.cta_smem > 0)
+        e = cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, p.cta_smem);
+    if (e == cudaSuccess && p.hist_smem > 0)
+        e = cudaFuncSetAttribute(k_eval_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, p.hist_smem);
     return e;
 }
 
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st)
 {
+    // The evaluation kernels are independent: the binary pass (bandwidth bound)
+    // runs on `st`, the non-binary classes on side streams, joined before the
+    // selection.  The same fork/join shape is recorded by graph capture.
     if (o.xhat || o.s || o.dc) k_fill_outputs<<<grid_for(d.n, 256), 256, 0, st>>>(d, o);
-    if (p.n_small) k_eval_small<<<p.n_small, kEvalThreads, 0, st>>>(d, p.tiles_small, o, gate);
-    if (p.n_cta) k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, st>>>(d, p.tiles_cta, o, p.n_small, gate);
-    if (p.n_hist_tiles) k_eval_hist<<<p.n_hist_tiles, kHistThreads, p.hist_smem, st>>>(d, p.tiles_hist, o, gate);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_eval(const Dev &d, const LaunchPlan &p, const VarOut &o, cudaStream_t st)
-{
-    return launch_eval_gated(d, p, o, 0, st);
+    cudaError_t e = cudaEventRecord(p.ev_fork, st);
+    const bool side[3] = {p.n_nb > 0, p.n_cta > 0, p.n_hist_tiles > 0};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (side[k]) e = cudaStreamWaitEvent(p.side[k], p.ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    if (p.n_bin) k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.tiles_bin, o, gate);
+    if (p.n_nb) k_eval_nb<<<p.n_nb, kNbThreads, 0, p.side[0]>>>(d, p.tiles_nb, o, p.slot_nb, gate);
+    if (p.n_cta) k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
+    if (p.n_hist_tiles) k_eval_hist<<<p.n_hist_tiles, kHistThreads, p.hist_smem, p.side[2]>>>(d, p.tiles_hist, o, gate);
+    e = cudaGetLastError();
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        if (!side[k]) continue;
+        e = cudaEventRecord(p.ev_join[k], p.side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p.ev_join[k], 0);
+    }
+    return e;
 }
 
 cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st)
@@ -1192,15 +1771,11 @@ cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_select(const Dev &d, cudaStream_t st) { return launch_select_gated(d, 0, st); }
-
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st)
 {
     k_apply<<<p.apply_blocks, kApplyThreads, 0, st>>>(d, gate);
     return cudaGetLastError();
 }
-
-cudaError_t launch_apply(const Dev &d, const LaunchPlan &p, cudaStream_t st) { return launch_apply_gated(d, p, 0, st); }
 
 cudaError_t launch_set_move(const Dev &d, int var, double nv, cudaStream_t st)
 {
@@ -1210,7 +1785,7 @@ cudaError_t launch_set_move(const Dev &d, int var, double nv, cudaStream_t st)
 
 cudaError_t launch_residuals(const Dev &d, cudaStream_t st)
 {
-    k_residuals<<<grid_for(d.m, 128, 152 * 16), 128, 0, st>>>(d);
+    k_residuals<<<grid_for((long long)d.m * 32, 256, 152 * 8), 256, 0, st>>>(d);
     return cudaGetLastError();
 }
 
@@ -1223,12 +1798,6 @@ cudaError_t launch_finish_set_state(const Dev &d, long long iter, long long best
 cudaError_t launch_begin_run(const Dev &d, long long max_iters, int stop_at_feasible, cudaStream_t st)
 {
     k_begin_run<<<1, 1, 0, st>>>(d, max_iters, stop_at_feasible);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pack_w(const Dev &d, const int *w, cudaStream_t st)
-{
-    k_pack_w<<<grid_for(d.m, 256), 256, 0, st>>>(d, w);
     return cudaGetLastError();
 }
 
@@ -1247,12 +1816,6 @@ cudaError_t launch_unpack_r(const Dev &d, double *r, cudaStream_t st)
 cudaError_t launch_tabu_convert(int n, const int *a, long long *b, cudaStream_t st)
 {
     k_widen<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tabu_narrow(int n, const long long *a, int *b, cudaStream_t st)
-{
-    k_narrow<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
     return cudaGetLastError();
 }
 
