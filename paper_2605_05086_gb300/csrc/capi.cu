@@ -433,7 +433,19 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         const int base = kind_base[k], cnt = kind_base[k + 1] - base;
         if (cnt == 0) continue;
         if (k == T_NB) {
-            for (int b = 0; b < cnt; b += kNbThreads) tiles_nb.push_back(Tile{k, base + b, base + std::min(cnt, b + kNbThreads), 0});
+            // consecutive columns while the tile keeps at most kNbTileCols columns
+            // and kNbTileEntries nonzeros (its queue holds two halves per nonzero)
+            int start = base, ent = 0;
+            for (int q = base; q < base + cnt; ++q) {
+                const int len = (ci_ptr[q + 1] - ci_ptr[q]) + (cf_ptr[q + 1] - cf_ptr[q]);
+                if (q > start && (ent + len > kNbTileEntries || q - start >= kNbTileCols)) {
+                    tiles_nb.push_back(Tile{k, start, q, 0});
+                    start = q;
+                    ent = 0;
+                }
+                ent += len;
+            }
+            tiles_nb.push_back(Tile{k, start, base + cnt, 0});
         } else if (k == T_NB_CTA) {
             for (int b = 0; b < cnt; ++b) {
                 max_cta_n = std::max(max_cta_n, cta_n[b]);
@@ -548,7 +560,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
     LaunchPlan &pl = h->plan;
     pl.tiles_bin = tb_d; pl.n_bin = n_tb;
-    pl.tiles_nb = tn_d; pl.n_nb = n_tn; pl.nb_smem = 0;
+    pl.tiles_nb = tn_d; pl.n_nb = n_tn; pl.nb_smem = n_tn ? 2 * kNbTileEntries * 4 : 0;
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
     pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);
     pl.slot_nb = n_tb; pl.slot_cta = n_tb + n_tn;

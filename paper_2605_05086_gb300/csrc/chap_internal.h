@@ -218,7 +218,8 @@ constexpr int kBinChunk = 2048;         // nonzeros staged in shared memory per 
 constexpr int kBinTileEntries = 4096;   // target nonzeros of one binary tile
 constexpr int kBinMaxCols = 1024;       // columns of one binary tile
 constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
-constexpr int kNbThreads = 128;         // short non-binary columns per CTA (one thread each)
+constexpr int kNbTileCols = 256;        // short non-binary columns of one tile (one finalizing thread each)
+constexpr int kNbTileEntries = 4096;    // nonzeros of one short non-binary tile (queue: 2 halves each)
 constexpr int kTileMaxCols = 64;        // columns of one non-binary tile
 constexpr int kTileSlots = 4096;        // sort-entry slots (16 B) of one non-binary tile
 constexpr int kTileEntries = 2048;      // nonzeros of one non-binary tile (its exact-pass queue holds 2 per nonzero)

@@ -1101,133 +1101,219 @@ __device__ void lane_sort(const Dev &d, const VarOut &o, const TileCol &t, const
     if (lane == 0) finish_column(d, o, t.c, vb, best);
 }
 
-// Short non-binary columns (at most kWarpSortMax breakpoint entries), one
-// thread per column.  After filtering, such a column has a handful of entries
-// inside [l, u], so a sequential pass per column beats any lane-parallel
-// network: the thread walks its nonzeros (row states gathered four at a time),
-// classifies every half by products, computes the exact breakpoint of the few
-// undecided halves into the column's list (scratch), insertion-sorts the list
-// by (t, marker), scans it and keeps the best admissible entry.
-// Exact breakpoint of one undecided half: the entry (type 0: none) and the
-// Algorithm 1 scalar increments.  Out of line: a few percent of the halves
-// take it, and a single copy keeps the streaming loop small.
-struct ExactOut {
-    unsigned long long key;
-    long long D;
-    long long beta, alpha;
-    int beta_c, alpha_c;
-    int type;
+// Short non-binary columns (at most kWarpSortMax breakpoint entries): a tile of
+// up to kNbTileCols consecutive columns per CTA, three converged phases.
+//  1. The tile's nonzeros are streamed in aligned groups of 8 per thread (as in
+//     the binary pass); every half is classified by products: its Algorithm 1
+//     scalars are accumulated, and the few halves whose breakpoint may lie in
+//     [l, u] are appended to a shared-memory queue.
+//  2. The queued halves (compacted: all lanes busy) get their exact breakpoint;
+//     entries inside [l, u] go to the column's list in the scratch.
+//  3. One thread per column: insertion sort of its short list by (t, marker)
+//     (a segmented sort with one segment per thread), scan, argmax.
+struct NbShared {
+    ColCtx ctx[kNbTileCols];
+    long long beta[kNbTileCols], alpha[kNbTileCols];
+    int beta_c[kNbTileCols], alpha_c[kNbTileCols], cnt[kNbTileCols];
+    int pi[kNbTileCols + 1], pf[kNbTileCols + 1];
+    int qn;
 };
 
-__device__ __noinline__ ExactOut exact_half(const ColCtx *c, int fp, long long ri, long long ai, double r, double a,
-                                            double m, double mo, int w)
+__device__ __forceinline__ void nb_flush(NbShared &S, int col, Acc &a)
 {
-    Acc acc{0, 0, 0, 0};
-    Half h;
-    h.type = 0;
-    if (fp) fp_half_exact(r, a, m, mo, w, *c, acc, h);
-    else int_half_exact(ri, ai, w, *c, acc, h);
-    return ExactOut{h.key, h.D, acc.beta, acc.alpha, acc.beta_c, acc.alpha_c, h.type};
+    if (a.beta) atomicAdd(reinterpret_cast<unsigned long long *>(&S.beta[col]), (unsigned long long)a.beta);
+    if (a.alpha) atomicAdd(reinterpret_cast<unsigned long long *>(&S.alpha[col]), (unsigned long long)a.alpha);
+    if (a.beta_c) atomicAdd(&S.beta_c[col], a.beta_c);
+    if (a.alpha_c) atomicAdd(&S.alpha_c[col], a.alpha_c);
+    a = Acc{0, 0, 0, 0};
 }
 
-__device__ __forceinline__ void take_exact(const ExactOut &x, Acc &acc, SEnt *list, int &cnt)
+// queue item: nonzero index inside the part, column, part (1 = non-integral rows), half
+__device__ __forceinline__ unsigned nb_item(int el, int col, int part, int half)
 {
-    acc.beta += x.beta;
-    acc.alpha += x.alpha;
-    acc.beta_c += x.beta_c;
-    acc.alpha_c += x.alpha_c;
-    if (x.type != 0) list[cnt++] = SEnt{x.key, (int)x.D, x.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
+    return ((unsigned)el << 10) | ((unsigned)col << 2) | ((unsigned)part << 1) | (unsigned)half;
 }
 
-__global__ void __launch_bounds__(kNbThreads, 6) k_eval_nb(Dev d, const Tile *tiles, VarOut o, int slot0, int gate)
+template <bool FP>
+__device__ __forceinline__ void nb_stream(const Dev &d, NbShared &S, int nc, unsigned *queue)
+{
+    const int *s_ptr = FP ? S.pf : S.pi;
+    const int E0 = s_ptr[0], E1 = s_ptr[nc];
+    const int g1 = (E1 + 7) >> 3;
+    for (int g = (E0 >> 3) + threadIdx.x; g < g1; g += blockDim.x) {
+        const int eb = g << 3;
+        int rows[8];
+        {
+            const int4 *rp = reinterpret_cast<const int4 *>((FP ? d.cf_row : d.ci_row) + eb);
+            const int4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+            rows[0] = r0.x; rows[1] = r0.y; rows[2] = r0.z; rows[3] = r0.w;
+            rows[4] = r1.x; rows[5] = r1.y; rows[6] = r1.z; rows[7] = r1.w;
+        }
+        double dv[8];
+        int iv[8];
+        if (FP) {
+            const double2 *vp = reinterpret_cast<const double2 *>(d.cf_val + eb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { const double2 v = __ldg(vp + k); dv[2 * k] = v.x; dv[2 * k + 1] = v.y; }
+        } else {
+            const int4 *vp = reinterpret_cast<const int4 *>(d.ci_val + eb);
+            const int4 v0 = __ldg(vp), v1 = __ldg(vp + 1);
+            iv[0] = v0.x; iv[1] = v0.y; iv[2] = v0.z; iv[3] = v0.w;
+            iv[4] = v1.x; iv[5] = v1.y; iv[6] = v1.z; iv[7] = v1.w;
+        }
+        int col = find_col(s_ptr, nc, max(eb, E0));
+        ClsCtx c = cls_of(S.ctx[col]);
+        Acc acc{0, 0, 0, 0};
+        constexpr int B = FP ? 4 : 8;
+#pragma unroll
+        for (int b0 = 0; b0 < 8; b0 += B) {
+            int4 st0[B], st1[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int e = eb + b0 + q;
+                if (e >= E0 && e < E1) {
+                    const int4 *pp = reinterpret_cast<const int4 *>(d.rs + rows[b0 + q]);
+                    st0[q] = __ldg(pp);
+                    if (FP) st1[q] = __ldg(pp + 1);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int e = eb + b0 + q;
+                if (e < E0 || e >= E1) continue;
+                if (s_ptr[col + 1] <= e) {
+                    while (s_ptr[col + 1] <= e) { nb_flush(S, col, acc); ++col; }
+                    c = cls_of(S.ctx[col]);
+                }
+                bool q1, q2 = false;
+                if (FP) {
+                    const double a = dv[b0 + q];
+                    const double r = i4_double_lo(st0[q]), m1 = i4_double_lo(st1[q]), m2 = i4_double_hi(st1[q]);
+                    q1 = classify_fp(r, a, m1, m2, st0[q].z, c, acc);
+                    if (st0[q].w >= 0) q2 = classify_fp(dflip(r), dflip(a), m2, m1, st0[q].w, c, acc);
+                } else {
+                    const long long a = iv[b0 + q];
+                    const long long r = row_r(st0[q]);
+                    q1 = classify_int(r, a, st0[q].z, c, acc);
+                    if (st0[q].w >= 0) q2 = classify_int(-r, -a, st0[q].w, c, acc);
+                }
+                if (q1 | q2) {
+                    int pos = atomicAdd(&S.qn, (int)q1 + (int)q2);
+                    if (q1) queue[pos++] = nb_item(e - E0, col, FP ? 1 : 0, 0);
+                    if (q2) queue[pos] = nb_item(e - E0, col, FP ? 1 : 0, 1);
+                }
+            }
+        }
+        nb_flush(S, col, acc);
+    }
+}
+
+__global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, const Tile *tiles, VarOut o, int slot0, int gate)
 {
     if (gated_done(d, gate)) return;
-    __shared__ ColCtx s_ctx[kNbThreads];
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned *queue = reinterpret_cast<unsigned *>(smem);
+    __shared__ NbShared S;
     const Tile tl = tiles[blockIdx.x];
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
-    Cand best{0, kNoVar, 0, 0.0};
-    const int q = tl.begin + threadIdx.x;
-    if (q < tl.end) {
-        ColCtx &c = s_ctx[threadIdx.x];
-        c = make_col(d, q, iter);
-        const ClsCtx k = cls_of(c);
+    const int nc = tl.end - tl.begin;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int q = tl.begin + c;
+        const ColCtx cc = make_col(d, q, iter);
+        S.ctx[c] = cc;
+        S.beta[c] = 0; S.alpha[c] = 0; S.beta_c[c] = 0; S.alpha_c[c] = 0;
         SEnt *list = d.lists + __ldg(d.list_off + (q - d.nb_pos0));
-        int cnt = 0;
-        const double l = __ldg(d.lb + c.j), u = __ldg(d.ub + c.j);
-        if (isfinite(l)) list[cnt++] = SEnt{c.kl, 0, make_aux(0, 0)};
-        if (isfinite(u)) list[cnt++] = SEnt{c.ku, 0, make_aux(0, 0)};
+        const double l = __ldg(d.lb + cc.j), u = __ldg(d.ub + cc.j);
+        int n = 0;
+        if (isfinite(l)) list[n++] = SEnt{cc.kl, 0, make_aux(0, 0)};
+        if (isfinite(u)) list[n++] = SEnt{cc.ku, 0, make_aux(0, 0)};
+        S.cnt[c] = n;
+    }
+    for (int c = threadIdx.x; c <= nc; c += blockDim.x) {
+        S.pi[c] = __ldg(d.ci_ptr + tl.begin + c);
+        S.pf[c] = __ldg(d.cf_ptr + tl.begin + c);
+    }
+    if (threadIdx.x == 0) S.qn = 0;
+    __syncthreads();
+    nb_stream<false>(d, S, nc, queue);
+    nb_stream<true>(d, S, nc, queue);
+    __syncthreads();
+    // phase 2: exact breakpoints of the queued halves
+    const int qn = S.qn;
+    for (int k = threadIdx.x; k < qn; k += blockDim.x) {
+        const unsigned it = queue[k];
+        const int half = it & 1, part = (it >> 1) & 1, col = (it >> 2) & 255, el = (int)(it >> 10);
+        const ColCtx &c = S.ctx[col];
         Acc acc{0, 0, 0, 0};
-        for (int v0 = 0; v0 < c.nI; v0 += 4) {
-            int rows[4], av[4];
-            int4 st[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (v0 + t < c.nI) { rows[t] = __ldg(d.ci_row + c.ci0 + v0 + t); av[t] = __ldg(d.ci_val + c.ci0 + v0 + t); }
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (v0 + t < c.nI) st[t] = ld_row16(d.rs + rows[t]);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (v0 + t >= c.nI) break;
-                const long long r = row_r(st[t]), a = av[t];
-                if (classify_int(r, a, st[t].z, k, acc))
-                    take_exact(exact_half(&c, 0, r, a, 0.0, 0.0, 0.0, 0.0, st[t].z), acc, list, cnt);
-                if (st[t].w >= 0 && classify_int(-r, -a, st[t].w, k, acc))
-                    take_exact(exact_half(&c, 0, -r, -a, 0.0, 0.0, 0.0, 0.0, st[t].w), acc, list, cnt);
-            }
+        Half h;
+        h.type = 0;
+        if (part == 0) {
+            const int e = S.pi[0] + el;
+            const int4 st = ld_row16(d.rs + __ldg(d.ci_row + e));
+            const long long a = __ldg(d.ci_val + e);
+            const long long r = row_r(st);
+            if (half == 0) int_half_exact(r, a, st.z, c, acc, h);
+            else int_half_exact(-r, -a, st.w, c, acc, h);
+        } else {
+            const int e = S.pf[0] + el;
+            const int4 *p = reinterpret_cast<const int4 *>(d.rs + __ldg(d.cf_row + e));
+            const double a = __ldg(d.cf_val + e);
+            const int4 s0 = __ldg(p), s1 = __ldg(p + 1);
+            const double r = i4_double_lo(s0), m1 = i4_double_lo(s1), m2 = i4_double_hi(s1);
+            if (half == 0) fp_half_exact(r, a, m1, m2, s0.z, c, acc, h);
+            else fp_half_exact(dflip(r), dflip(a), m2, m1, s0.w, c, acc, h);
         }
-        for (int v0 = 0; v0 < c.nF; v0 += 4) {
-            int rows[4];
-            double av[4];
-            int4 s0[4], s1[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (v0 + t < c.nF) { rows[t] = __ldg(d.cf_row + c.cf0 + v0 + t); av[t] = __ldg(d.cf_val + c.cf0 + v0 + t); }
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (v0 + t < c.nF) {
-                    const int4 *p = reinterpret_cast<const int4 *>(d.rs + rows[t]);
-                    s0[t] = __ldg(p);
-                    s1[t] = __ldg(p + 1);
-                }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (v0 + t >= c.nF) break;
-                const double a = av[t];
-                const double r = i4_double_lo(s0[t]), m1 = i4_double_lo(s1[t]), m2 = i4_double_hi(s1[t]);
-                if (classify_fp(r, a, m1, m2, s0[t].z, k, acc))
-                    take_exact(exact_half(&c, 1, 0, 0, r, a, m1, m2, s0[t].z), acc, list, cnt);
-                if (s0[t].w >= 0 && classify_fp(dflip(r), dflip(a), m2, m1, s0[t].w, k, acc))
-                    take_exact(exact_half(&c, 1, 0, 0, dflip(r), dflip(a), m2, m1, s0[t].w), acc, list, cnt);
-            }
+        nb_flush(S, col, acc);
+        if (h.type != 0) {
+            SEnt *list = d.lists + __ldg(d.list_off + (tl.begin + col - d.nb_pos0));
+            list[atomicAdd(&S.cnt[col], 1)] = SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
         }
-        // insertion sort by (t, marker)
+    }
+    __syncthreads();
+    // phase 3: one thread per column
+    Cand best{0, kNoVar, 0, 0.0};
+    for (int cidx = threadIdx.x; cidx < nc; cidx += blockDim.x) {
+        const ColCtx &c = S.ctx[cidx];
+        SEnt *list = d.lists + __ldg(d.list_off + (tl.begin + cidx - d.nb_pos0));
+        const int cnt = S.cnt[cidx];
         for (int i = 1; i < cnt; ++i) {
-            const SEnt e = list[i];
+            const int4 ri = __ldcg(reinterpret_cast<const int4 *>(list + i));
+            const unsigned long long ek = ((unsigned long long)(unsigned)ri.y << 32) | (unsigned)ri.x;
+            const unsigned ea = (unsigned)ri.w;
             int j = i - 1;
-            while (j >= 0 && entry_less(e.key, e.aux, list[j].key, list[j].aux)) { list[j + 1] = list[j]; --j; }
-            list[j + 1] = e;
+            while (j >= 0) {
+                const int4 rj = __ldcg(reinterpret_cast<const int4 *>(list + j));
+                const unsigned long long jk = ((unsigned long long)(unsigned)rj.y << 32) | (unsigned)rj.x;
+                if (!entry_less(ek, ea, jk, (unsigned)rj.w)) break;
+                *reinterpret_cast<int4 *>(list + j + 1) = rj;
+                --j;
+            }
+            *reinterpret_cast<int4 *>(list + j + 1) = ri;
         }
-        // scan and argmax (Algorithm 1, phases 3-4)
+        const long long beta = S.beta[cidx], alpha = S.alpha[cidx];
+        const int bc = S.beta_c[cidx], ac = S.alpha_c[cidx];
         long long P = 0;
         int Pc = 0;
         VCand vb{0, 0ull, 0, 0};
         unsigned long long kprev = 0ull;
+        int4 cur = cnt > 0 ? __ldcg(reinterpret_cast<const int4 *>(list)) : make_int4(0, 0, 0, 0);
         for (int i = 0; i < cnt; ++i) {
-            const SEnt e = list[i];
-            P += e.del;
-            Pc += aux_dc(e.aux);
-            const unsigned long long knext = i + 1 < cnt ? list[i + 1].key : kPadKey;
-            const unsigned anext = i + 1 < cnt ? list[i + 1].aux : make_aux(1, 0);
-            if (is_candidate(e.key, e.aux, kprev, i > 0, knext, anext)) {
-                const bool post = aux_post(e.aux) != 0;
-                const long long Pi = P - (post ? e.del : 0);
-                const int Pci = Pc - (post ? aux_dc(e.aux) : 0);
-                const bool right = e.key > c.kxb;
-                consider(vb, c, e.key, acc.beta + Pi + (right ? acc.alpha : 0),
-                         acc.beta_c + Pci + (right ? acc.alpha_c : 0), nviol, bestnv);
+            const int4 nxt = i + 1 < cnt ? __ldcg(reinterpret_cast<const int4 *>(list + i + 1)) : make_int4(-1, -1, 0, (int)make_aux(1, 0));
+            const unsigned long long ek = ((unsigned long long)(unsigned)cur.y << 32) | (unsigned)cur.x;
+            const unsigned ea = (unsigned)cur.w;
+            const long long del = cur.z;
+            P += del;
+            Pc += aux_dc(ea);
+            const unsigned long long knext = ((unsigned long long)(unsigned)nxt.y << 32) | (unsigned)nxt.x;
+            if (is_candidate(ek, ea, kprev, i > 0, knext, (unsigned)nxt.w)) {
+                const bool post = aux_post(ea) != 0;
+                const long long Pi = P - (post ? del : 0);
+                const int Pci = Pc - (post ? aux_dc(ea) : 0);
+                const bool right = ek > c.kxb;
+                consider(vb, c, ek, beta + Pi + (right ? alpha : 0), bc + Pci + (right ? ac : 0), nviol, bestnv);
             }
-            kprev = e.key;
+            kprev = ek;
+            cur = nxt;
         }
         finish_column(d, o, c, vb, best);
     }
@@ -1753,7 +1839,7 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
         if (side[k]) e = cudaStreamWaitEvent(p.side[k], p.ev_fork, 0);
     if (e != cudaSuccess) return e;
     if (p.n_bin) k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.tiles_bin, o, gate);
-    if (p.n_nb) k_eval_nb<<<p.n_nb, kNbThreads, 0, p.side[0]>>>(d, p.tiles_nb, o, p.slot_nb, gate);
+    if (p.n_nb) k_eval_nb<<<p.n_nb, kEvalThreads, p.nb_smem, p.side[0]>>>(d, p.tiles_nb, o, p.slot_nb, gate);
     if (p.n_cta) k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
     if (p.n_hist_tiles) k_eval_hist<<<p.n_hist_tiles, kHistThreads, p.hist_smem, p.side[2]>>>(d, p.tiles_hist, o, gate);
     e = cudaGetLastError();
