@@ -327,8 +327,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
 
     // ---- classify variables
     //  binary: streamed by T_BIN tiles; other columns by breakpoint entries (one
-    //  per normalised half plus the bounds): packed / warp bitonic in T_NB tiles
-    //  (<= kWarpSortMax), then multi-CTA counting sort (integer, domain <=
+    //  per normalised half plus the bounds): one warp per column (T_NB,
+    //  <= kWarpSortMax), then multi-CTA counting sort (integer, domain <=
     //  kHistMaxDomain) or CTA bitonic (<= kCtaMaxEntries).
     std::vector<std::vector<int>> kind_vars(T_NUM_KINDS);
     std::vector<int> fixed_vars;
@@ -363,8 +363,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         kind_vars[k].push_back(j);
     }
     {
-        // short columns are evaluated one per thread: order them by entry count so
-        // that the threads of a warp do similar work
+        // short columns (one warp each, strided over the grid): order them by
+        // entry count so that the CTAs of one wave get similar mixes
         std::vector<int> ord(nb_cap.size());
         for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
         std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return nb_cap[x] < nb_cap[y]; });
@@ -383,8 +383,6 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
     kind_base[T_NUM_KINDS] = (int)var_list.size();
     var_list.insert(var_list.end(), fixed_vars.begin(), fixed_vars.end());
-    std::vector<long long> nb_off(nb_cap.size() + 1, 0);  // list offsets of the T_NB columns
-    for (size_t k = 0; k < nb_cap.size(); ++k) nb_off[k + 1] = nb_off[k] + nb_cap[k];
     std::vector<int> vpos(n);
     for (int q = 0; q < n; ++q) vpos[var_list[q]] = q;
 
@@ -409,7 +407,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
 
     // ---- work tiles
-    std::vector<Tile> tiles_bin, tiles_nb, tiles_cta, tiles_hist;
+    std::vector<Tile> tiles_bin, tiles_cta, tiles_hist;
     std::vector<HistCol> hcols;
     int max_cta_n = 0, max_hist_d = 0;
     int64_t hist_bins = 0;
@@ -433,19 +431,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         const int base = kind_base[k], cnt = kind_base[k + 1] - base;
         if (cnt == 0) continue;
         if (k == T_NB) {
-            // consecutive columns while the tile keeps at most kNbTileCols columns
-            // and kNbTileEntries nonzeros (its queue holds two halves per nonzero)
-            int start = base, ent = 0;
-            for (int q = base; q < base + cnt; ++q) {
-                const int len = (ci_ptr[q + 1] - ci_ptr[q]) + (cf_ptr[q + 1] - cf_ptr[q]);
-                if (q > start && (ent + len > kNbTileEntries || q - start >= kNbTileCols)) {
-                    tiles_nb.push_back(Tile{k, start, q, 0});
-                    start = q;
-                    ent = 0;
-                }
-                ent += len;
-            }
-            tiles_nb.push_back(Tile{k, start, base + cnt, 0});
+            continue;  // one warp per column, no tiles
         } else if (k == T_NB_CTA) {
             for (int b = 0; b < cnt; ++b) {
                 max_cta_n = std::max(max_cta_n, cta_n[b]);
@@ -469,7 +455,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
             }
         }
     }
-    const int n_tb = (int)tiles_bin.size(), n_tn = (int)tiles_nb.size(), n_tc = (int)tiles_cta.size();
+    const int nb_cols = kind_base[T_NB + 1] - kind_base[T_NB];
+    const int n_tn = nb_cols > 0 ? nb_grid_size(nb_cols) : 0;
+    const int n_tb = (int)tiles_bin.size(), n_tc = (int)tiles_cta.size();
     const int slot_hist = n_tb + n_tn + n_tc;
     for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = slot_hist + (int)q;
     const int n_bb = slot_hist + (int)hcols.size();
@@ -501,16 +489,12 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     int *vpos_d = dalloc<int>(h, n);
     d.block_best = dalloc<Cand>(h, n_bb);
     d.n_block_best = n_bb;
-    Tile *tb_d = dalloc<Tile>(h, tiles_bin.size()), *tn_d = dalloc<Tile>(h, tiles_nb.size());
+    Tile *tb_d = dalloc<Tile>(h, tiles_bin.size());
     Tile *tc_d = dalloc<Tile>(h, tiles_cta.size());
     Tile *th_d = dalloc<Tile>(h, tiles_hist.size());
     HistCol *hc_d = dalloc<HistCol>(h, hcols.size());
     d.hbins = dalloc<HBin>(h, hist_bins);
     d.hacc = dalloc<HistAcc>(h, hcols.size());
-    d.lists = dalloc<SEntry>(h, (size_t)nb_off.back());
-    long long *nb_off_d = dalloc<long long>(h, nb_off.size());
-    d.list_off = nb_off_d;
-    d.nb_pos0 = kind_base[T_NB];
     h->t_xhat = dalloc<double>(h, n);
     h->t_s = dalloc<long long>(h, n);
     h->t_dc = dalloc<int>(h, n);
@@ -519,8 +503,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     h->t_tabu = dalloc<long long>(h, n);
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && row_ptr_d && col_idx_d &&
               row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.rs &&
-              d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tb_d && tn_d && tc_d && th_d && hc_d &&
-              d.hbins && d.hacc && d.lists && nb_off_d && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
+              d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tb_d && tc_d && th_d && hc_d &&
+              d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
     if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
     for (int k = 0; k < 3 && ok; ++k)
@@ -550,17 +534,16 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     UP(rhs_d, rhs.data(), m); UP(eps_d, eps.data(), m); UP(rint_d, rint.data(), m); UP(nrb_d, h->nrow_base.data(), m);
     UP(vt_d, p->vtype, n); UP(lb_d, p->lb, n); UP(ub_d, p->ub, n); UP(obj_d, h->obj.data(), n);
     UP(vl_d, var_list.data(), var_list.size()); UP(vpos_d, vpos.data(), n);
-    UP(tb_d, tiles_bin.data(), tiles_bin.size()); UP(tn_d, tiles_nb.data(), tiles_nb.size());
+    UP(tb_d, tiles_bin.data(), tiles_bin.size());
     UP(tc_d, tiles_cta.data(), tiles_cta.size());
     UP(th_d, tiles_hist.data(), tiles_hist.size()); UP(hc_d, hcols.data(), hcols.size());
-    UP(nb_off_d, nb_off.data(), nb_off.size());
 #undef UP
     if (e == cudaSuccess && hist_bins > 0) e = cudaMemsetAsync(d.hbins, 0, sizeof(HBin) * hist_bins, st);
     if (e == cudaSuccess && !hcols.empty()) e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
     LaunchPlan &pl = h->plan;
     pl.tiles_bin = tb_d; pl.n_bin = n_tb;
-    pl.tiles_nb = tn_d; pl.n_nb = n_tn; pl.nb_smem = n_tn ? 2 * kNbTileEntries * 4 : 0;
+    pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn;
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
     pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);
     pl.slot_nb = n_tb; pl.slot_cta = n_tb + n_tn;

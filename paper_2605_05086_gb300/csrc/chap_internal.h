@@ -76,7 +76,7 @@ struct __align__(16) Ctl {
 // Work tiles of the best-shift pass.  A tile covers var_list[begin, end).
 enum TileKind : int {
     T_BIN = 0,                // binary flips: consecutive columns streamed by one CTA
-    T_NB,                     // short breakpoint lists: packed / warp bitonic sorts
+    T_NB,                     // short breakpoint lists: one warp per column
     T_NB_CTA,                 // CTA bitonic sort in shared memory
     T_NB_HIST,                // multi-CTA counting sort (long integer columns)
     T_NUM_KINDS
@@ -150,16 +150,10 @@ struct Dev {
     HBin *hbins;
     HistAcc *hacc;
     const HistCol *hcols;
-    // scratch of the short non-binary columns: the breakpoint entries inside
-    // [l, u] of position q are written to lists[list_off[q - nb_pos0] ...]
-    struct SEntry *lists;
-    const long long *list_off;
-    int nb_pos0;
-    int pad2;
 };
 
-// Breakpoint entry of a short non-binary column: key (t in order-preserving
-// form), score delta (|delta| <= 2w < 2^31), aux = post marker and count delta.
+// Breakpoint entry staged in shared memory: key (t in order-preserving form),
+// score delta (|delta| <= 2w < 2^31), aux = post marker and count delta.
 struct __align__(16) SEntry {
     unsigned long long key;
     int del;
@@ -176,9 +170,8 @@ struct VarOut {
 struct LaunchPlan {
     const Tile *tiles_bin;     // device
     int n_bin;
-    const Tile *tiles_nb;      // non-binary tiles (breakpoint lists of <= kWarpSortMax entries)
-    int n_nb;
-    int nb_smem;
+    int nb_q0, nb_cols;        // positions of the short non-binary columns (<= kWarpSortMax entries)
+    int nb_grid;               // CTAs of the persistent warp-per-column kernel (0: no such column)
     const Tile *tiles_cta;
     int n_cta;
     int cta_smem;              // dynamic shared memory of the CTA-sort kernel
@@ -194,6 +187,7 @@ struct LaunchPlan {
 // Kernel launchers (kernels.cu).  All are asynchronous on `st`; `gate` makes a
 // kernel return at once when the run's done flag is set (graph replays).
 cudaError_t setup_kernel_attributes(const LaunchPlan &p);
+int nb_grid_size(int ncols);   // persistent grid of the short-column kernel on the current device
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
 cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st);
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
@@ -207,7 +201,6 @@ cudaError_t launch_tabu_convert(int n, const int *src32, long long *dst64, cudaS
 
 // Sizes used by both sides.
 constexpr int kEvalThreads = 256;
-constexpr int kWarpStageCap = 128;      // entries staged per warp (K <= 4)
 constexpr int kCtaMaxEntries = 8192;    // largest entry list sorted by one CTA
 constexpr int kCtaThreads = 512;
 constexpr int kHistMaxDomain = 4096;    // largest integer domain of the multi-CTA counting sort
@@ -218,10 +211,5 @@ constexpr int kBinChunk = 2048;         // nonzeros staged in shared memory per 
 constexpr int kBinTileEntries = 4096;   // target nonzeros of one binary tile
 constexpr int kBinMaxCols = 1024;       // columns of one binary tile
 constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
-constexpr int kNbTileCols = 256;        // short non-binary columns of one tile (one finalizing thread each)
-constexpr int kNbTileEntries = 4096;    // nonzeros of one short non-binary tile (queue: 2 halves each)
-constexpr int kTileMaxCols = 64;        // columns of one non-binary tile
-constexpr int kTileSlots = 4096;        // sort-entry slots (16 B) of one non-binary tile
-constexpr int kTileEntries = 2048;      // nonzeros of one non-binary tile (its exact-pass queue holds 2 per nonzero)
 
 }  // namespace chap

@@ -509,7 +509,7 @@ struct Half {
 // entry lands left of l (side -1: folded into beta), right of u (side +1:
 // dropped) or at key (side 0, compared with the bound keys here).
 __device__ __forceinline__ void half_case(bool viol, bool tight, bool apos, int side, unsigned long long key,
-                                          long long w, const ColCtx &c, Acc &acc, Half &h)
+                                          long long w, unsigned long long kl, unsigned long long ku, Acc &acc, Half &h)
 {
     h.type = 0;
     if (tight) {
@@ -528,7 +528,7 @@ __device__ __forceinline__ void half_case(bool viol, bool tight, bool apos, int 
         else { D = -2 * w; }
         type = 2;
     }
-    if (side == 0) side = key < c.kl ? -1 : (key > c.ku ? 1 : 0);
+    if (side == 0) side = key < kl ? -1 : (key > ku ? 1 : 0);
     if (side < 0) {
         acc.beta += D;
         acc.beta_c += (type == 1) ? -1 : 1;
@@ -552,11 +552,11 @@ __device__ __forceinline__ void int_half(long long r, long long a, long long w, 
     if (apos) side = (r > -c.lo * a) ? -1 : ((-r >= (c.hi + 1) * a) ? 1 : 0);
     else side = (-r >= (c.lo - 1) * a) ? -1 : ((-r < c.hi * a) ? 1 : 0);
     if (side != 0) {
-        half_case(viol, false, apos, side, 0ull, w, c, acc, h);
+        half_case(viol, false, apos, side, 0ull, w, c.kl, c.ku, acc, h);
         return;
     }
     const long long dd = apos ? floor_div(-r, a) : ceil_div(-r, a);
-    half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
+    half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c.kl, c.ku, acc, h);
 }
 
 // |x| with a relative error bound e and an absolute floor, for the certain
@@ -619,23 +619,23 @@ __device__ __forceinline__ void fp_half(double r, double a, double m, double mo,
     if (c.isint) {
         const int side = int_fp_side(m, a, apos, c);
         if (side != 0) {
-            half_case(viol, false, apos, side, 0ull, w, c, acc, h);
+            half_case(viol, false, apos, side, 0ull, w, c.kl, c.ku, acc, h);
             return;
         }
         const double q = __ddiv_rn(m, a);
         const long long dd = clamp_dd(apos ? __double2ll_rd(q) : __double2ll_ru(q));
-        half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
+        half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c.kl, c.ku, acc, h);
     } else {
         const bool near0 = !viol && !dneg(mo);  // |r| <= eps
         const int side = cont_fp_side(r, a, apos, c);
         if (side != 0) {
-            half_case(viol, near0, apos, side, 0ull, w, c, acc, h);
+            half_case(viol, near0, apos, side, 0ull, w, c.kl, c.ku, acc, h);
             return;
         }
         const double t = __dsub_rn(c.xb, __ddiv_rn(r, a));
         unsigned long long k = dkey(t);
         if (k == dkey(-0.0)) k = dkey(0.0);
-        half_case(viol, near0 || (!viol && k == c.kxb), apos, 0, k, w, c, acc, h);
+        half_case(viol, near0 || (!viol && k == c.kxb), apos, 0, k, w, c.kl, c.ku, acc, h);
     }
 }
 
@@ -703,63 +703,37 @@ __device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, u
     return !has_prev || kprev != k;
 }
 
-// ------------------------------------------- flat tiles of non-binary columns
+// ------------------------------------------------- short non-binary columns
 //
-// A tile is a run of consecutive positions (columns contiguous in both CSC
-// matrices).  All threads of the CTA stream the tile's nonzeros in aligned
-// groups of 8 (two 16-byte loads of row indices and coefficients per thread,
-// the row states of the group gathered together), generate the breakpoint
-// entries of Algorithm 1 and append the ones inside [l, u] to the column's
-// segment in shared memory.  Then each column's segment is sorted, scanned and
-// reduced: short segments by bitonic networks packed several to a warp (8 or
-// 16 lanes per column), longer ones by a whole warp with K entries per lane.
+// Columns with at most kWarpSortMax breakpoint entries (bounds included).  A
+// group of kGrp = 8 lanes evaluates one column, so one warp holds four columns
+// at a time; a persistent grid takes the warps' column quadruples in a strided
+// order.
+//  1. Classification.  The lanes of a group read the column's nonzeros
+//     coalesced (integral-row part, then the non-integral part), two per lane
+//     in flight, and gather their row states.  Every half is first placed by
+//     single-precision products with error margins (no division): a half
+//     whose breakpoint is certainly left of l or right of u only changes the
+//     scalars beta / alpha of Algorithm 1.  Integral and non-integral rows
+//     share this test (on an integral row m = -r exactly), so the lanes do not
+//     diverge by row type.
+//  2. The undecided halves (a few percent) go to a per-warp queue with their
+//     operands; whenever 32 are queued all lanes compute 32 exact breakpoints
+//     at once (FP64 divisions are slow on this part, so they are never issued
+//     for a single lane), and the entries inside [l, u] are appended to the
+//     column's list in shared memory.
+//  3. Each group sorts its list (bitonic over 8 lanes, 1, 2 or 4 entries per
+//     lane), prefix-scans it with shuffles and reduces it to the column's best
+//     admissible candidate.  A column whose list outgrows kGrpStage entries is
+//     evaluated again by the whole warp with a list of kWarpSortMax entries.
 
-struct TileCol {
-    ColCtx c;
-    long long beta, alpha;
-    int beta_c, alpha_c;
-    int cnt;          // entries in the column's list
-    int pad;
-    long long lbase;  // offset of the column's list in the scratch
-};
-
+constexpr int kNbWarps = kEvalThreads / 32;
+constexpr int kGrp = 8;                      // lanes per column
+constexpr int kGrpPerWarp = 32 / kGrp;       // columns per warp
+constexpr int kGrpStage = 4 * kGrp;          // list entries per column on the group path
+constexpr int kQCap = 32 + 4 * 32 - 1;      // queued halves per warp: < 32 left + one round of 4 halves per lane
+static_assert(kGrpPerWarp * kGrpStage == kWarpSortMax, "the whole-warp path reuses the group lists");
 using SEnt = SEntry;
-
-__device__ __forceinline__ void flush_acc(TileCol &t, Acc &a)
-{
-    if (a.beta) atomicAdd(reinterpret_cast<unsigned long long *>(&t.beta), (unsigned long long)a.beta);
-    if (a.alpha) atomicAdd(reinterpret_cast<unsigned long long *>(&t.alpha), (unsigned long long)a.alpha);
-    if (a.beta_c) atomicAdd(&t.beta_c, a.beta_c);
-    if (a.alpha_c) atomicAdd(&t.alpha_c, a.alpha_c);
-    a = Acc{0, 0, 0, 0};
-}
-
-// Exact breakpoint of one half whose side could not be decided by products.
-__device__ __forceinline__ void int_half_exact(long long r, long long a, long long w, const ColCtx &c, Acc &acc, Half &h)
-{
-    const bool viol = r > 0;
-    const bool apos = a > 0;
-    const long long dd = apos ? floor_div(-r, a) : ceil_div(-r, a);
-    half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
-}
-
-__device__ __forceinline__ void fp_half_exact(double r, double a, double m, double mo, long long w, const ColCtx &c,
-                                              Acc &acc, Half &h)
-{
-    const bool viol = dneg(m);
-    const bool apos = !dneg(a);
-    if (c.isint) {
-        const double q = __ddiv_rn(m, a);
-        const long long dd = clamp_dd(apos ? __double2ll_rd(q) : __double2ll_ru(q));
-        half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c, acc, h);
-    } else {
-        const bool near0 = !viol && !dneg(mo);
-        const double t = __dsub_rn(c.xb, __ddiv_rn(r, a));
-        unsigned long long k = dkey(t);
-        if (k == dkey(-0.0)) k = dkey(0.0);
-        half_case(viol, near0 || (!viol && k == c.kxb), apos, 0, k, w, c, acc, h);
-    }
-}
 
 // Algorithm 1 scalars of a half whose breakpoint is decided without its key:
 // tight, or certainly left of l (side -1) / right of u (side +1).
@@ -782,186 +756,127 @@ __device__ __forceinline__ void half_acc(bool viol, bool tight, bool apos, int s
     }
 }
 
-// What the classification needs of a column (kept in registers while streaming).
-struct ClsCtx {
-    long long lo, hi;
-    float lof, hif, dlf, duf, xaf;
-    bool isint, fok;
+// Undecided half (operands already negated for the second half of an "=" row):
+//  integral row:      x = r, a (int64);
+//  non-integral row:  x = eps - r (integer variable) or r (continuous), a (double bits),
+// meta = group | row kind << 2 | violated << 3.  A queued half of a continuous
+// variable is never "near 0" (|r| <= eps): those are decided by the pre-filter.
+struct __align__(8) QItem {
+    long long x, a;
+    int w, meta;
 };
 
-__device__ __forceinline__ ClsCtx cls_of(const ColCtx &c)
+struct __align__(16) NbWarp {
+    SEnt stage[kGrpPerWarp * kGrpStage];
+    QItem q[kQCap];                         // ring buffer
+    ColCtx ctx[kGrpPerWarp];
+    long long beta[kGrpPerWarp], alpha[kGrpPerWarp];
+    int beta_c[kGrpPerWarp], alpha_c[kGrpPerWarp], cnt[kGrpPerWarp];
+};
+constexpr int kNbSmem = kNbWarps * (int)sizeof(NbWarp);   // dynamic shared memory of k_eval_nb
+
+// Single-precision estimate of an int64 (relative error < 2^-23).
+__device__ __forceinline__ float ll_approx(long long v)
 {
-    return ClsCtx{c.lo, c.hi, c.lof, c.hif, c.dlf, c.duf, c.xaf, c.isint, c.fok};
+    return (v >= INT_MIN && v <= INT_MAX) ? (float)(int)v : __ll2float_rn(v);
 }
 
-// Cheap classification of one half (products only).  Returns true when the
-// half needs its exact breakpoint; otherwise its Algorithm 1 scalars are added.
-__device__ __forceinline__ bool classify_int(long long r, long long a, long long w, const ClsCtx &c, Acc &acc)
+// Place the breakpoint of a half by products: z / a against the thresholds
+// L (left of l) and U (right of u) of the column, a > 0 after normalisation.
+// Returns -1 / +1 when certain, else 0.
+__device__ __forceinline__ int side_of(float z, float a, float L, float U, float tol)
 {
-    const bool viol = r > 0;
-    const bool apos = a > 0;
-    int side;
-    if (apos) side = (r > -c.lo * a) ? -1 : ((-r >= (c.hi + 1) * a) ? 1 : 0);
-    else side = (-r >= (c.lo - 1) * a) ? -1 : ((-r < c.hi * a) ? 1 : 0);
-    if (side == 0) return true;
-    half_acc(viol, false, apos, side, w, acc);
-    return false;
+    const float P = L * a, Q = U * a;
+    if (z + slack(z) + tol < P - slack(P)) return -1;
+    if (z - slack(z) - tol > Q + slack(Q)) return 1;
+    return 0;
 }
 
-__device__ __forceinline__ bool classify_fp(double r, double a, double m, double mo, long long w, const ClsCtx &c,
-                                            Acc &acc)
+// Exact breakpoint of one queued half (Algorithm 1 case table, as int_half /
+// fp_half after an undecided side test).
+__device__ __forceinline__ void exact_item(const QItem &it, const ColCtx &ci, Acc &acc, Half &h)
 {
-    const bool viol = dneg(m);
-    const bool apos = !dneg(a);
-    bool ok = true;
-    const float af = approx_f(a, ok);
-    int side = 0;
-    if (c.isint) {
-        const float mf = approx_f(m, ok);
-        if (ok) {
-            if (apos) {
-                const float P = c.lof * af, Q = (c.hif + 1.0f) * af;  // t < l <=> m < lo a; t > u <=> m >= (hi+1) a
-                if (mf + slack(mf) < P - slack(P)) side = -1;
-                else if (mf - slack(mf) > Q + slack(Q)) side = 1;
-            } else {
-                const float P = (c.lof - 1.0f) * af, Q = c.hif * af;  // t < l <=> m >= (lo-1) a; t > u <=> m < hi a
-                if (mf - slack(mf) > P + slack(P)) side = -1;
-                else if (mf + slack(mf) < Q - slack(Q)) side = 1;
-            }
-        }
-        if (side == 0) return true;
-        half_acc(viol, false, apos, side, w, acc);
-        return false;
-    }
-    if (!viol && !dneg(mo)) {  // |r| <= eps: tight whatever t is
-        half_acc(false, true, apos, 0, w, acc);
-        return false;
-    }
-    ok = ok && c.fok;
-    const float rf = approx_f(r, ok);
-    if (ok) {
-        const float tol = c.xaf * fabsf(af) * 1.0e-10f;
-        const float P = c.dlf * af, Q = c.duf * af;  // t < l <=> r/a > xbar - l; t > u <=> r/a < xbar - u
-        if (apos) {
-            if (rf - slack(rf) - tol > P + slack(P)) side = -1;
-            else if (rf + slack(rf) + tol < Q - slack(Q)) side = 1;
+    const bool viol = ((it.meta >> 3) & 1) != 0;
+    bool apos, tight;
+    unsigned long long key;
+    if (((it.meta >> 2) & 1) == 0) {
+        const long long r = it.x, a = it.a;
+        apos = a > 0;
+        const long long dd = apos ? floor_div(-r, a) : ceil_div(-r, a);
+        tight = !viol && dd == 0;
+        key = ikey(ci.xbi + dd);
+    } else {
+        const double a = __longlong_as_double(it.a);
+        apos = !dneg(a);
+        if (ci.isint) {
+            const double q = __ddiv_rn(__longlong_as_double(it.x), a);
+            const long long dd = clamp_dd(apos ? __double2ll_rd(q) : __double2ll_ru(q));
+            tight = !viol && dd == 0;
+            key = ikey(ci.xbi + dd);
         } else {
-            if (rf + slack(rf) + tol < P - slack(P)) side = -1;
-            else if (rf - slack(rf) - tol > Q + slack(Q)) side = 1;
+            const double t = __dsub_rn(ci.xb, __ddiv_rn(__longlong_as_double(it.x), a));
+            key = dkey(t);
+            if (key == dkey(-0.0)) key = dkey(0.0);
+            tight = !viol && key == ci.kxb;
         }
     }
-    if (side == 0) return true;
-    half_acc(viol, false, apos, side, w, acc);
-    return false;
+    half_case(viol, tight, apos, 0, key, it.w, ci.kl, ci.ku, acc, h);
 }
 
-// Exact breakpoint of one undecided half: its Algorithm 1 scalars go to the
-// column's shared accumulators and its entry, when inside [l, u], to the
-// column's list.  Kept out of line: it runs for a few percent of the halves.
-__device__ __noinline__ void exact_put(const Dev &d, TileCol *t, bool fp, long long ri, long long ai, double r,
-                                       double a, double m, double mo, int w)
+// Exact pass over n <= 32 queued halves starting at ring position head, one per lane.
+__device__ __forceinline__ void flush_queue(NbWarp &W, int head, int n, int lane)
 {
-    Acc acc{0, 0, 0, 0};
-    Half h;
-    h.type = 0;
-    if (fp) fp_half_exact(r, a, m, mo, w, t->c, acc, h);
-    else int_half_exact(ri, ai, w, t->c, acc, h);
-    flush_acc(*t, acc);
-    if (h.type != 0) {
-        const int pos = atomicAdd(&t->cnt, 1);
-        d.lists[t->lbase + pos] = SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
-    }
-}
-
-// Stream one CSC part of a non-binary tile: aligned groups of 8 nonzeros per
-// thread, row states gathered together, halves classified by products.
-template <bool FP>
-__device__ __forceinline__ void nb_part(const Dev &d, TileCol *tc, int nc, const int *s_ptr)
-{
-    const int E0 = s_ptr[0], E1 = s_ptr[nc];
-    const int g1 = (E1 + 7) >> 3;
-    for (int g = (E0 >> 3) + threadIdx.x; g < g1; g += blockDim.x) {
-        const int eb = g << 3;
-        int rows[8];
-        {
-            const int4 *rp = reinterpret_cast<const int4 *>((FP ? d.cf_row : d.ci_row) + eb);
-            const int4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-            rows[0] = r0.x; rows[1] = r0.y; rows[2] = r0.z; rows[3] = r0.w;
-            rows[4] = r1.x; rows[5] = r1.y; rows[6] = r1.z; rows[7] = r1.w;
-        }
-        double dv[8];
-        int iv[8];
-        if (FP) {
-            const double2 *vp = reinterpret_cast<const double2 *>(d.cf_val + eb);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { const double2 v = __ldg(vp + k); dv[2 * k] = v.x; dv[2 * k + 1] = v.y; }
-        } else {
-            const int4 *vp = reinterpret_cast<const int4 *>(d.ci_val + eb);
-            const int4 v0 = __ldg(vp), v1 = __ldg(vp + 1);
-            iv[0] = v0.x; iv[1] = v0.y; iv[2] = v0.z; iv[3] = v0.w;
-            iv[4] = v1.x; iv[5] = v1.y; iv[6] = v1.z; iv[7] = v1.w;
-        }
-        int col = find_col(s_ptr, nc, max(eb, E0));
-        ClsCtx c = cls_of(tc[col].c);
+    if (lane < n) {
+        int pos = head + lane;
+        if (pos >= kQCap) pos -= kQCap;
+        const QItem it = W.q[pos];
+        const int g = it.meta & 3;
         Acc acc{0, 0, 0, 0};
-        constexpr int B = FP ? 4 : 8;
-#pragma unroll
-        for (int b0 = 0; b0 < 8; b0 += B) {
-            int4 st0[B], st1[B];
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int e = eb + b0 + q;
-                if (e >= E0 && e < E1) {
-                    const int4 *pp = reinterpret_cast<const int4 *>(d.rs + rows[b0 + q]);
-                    st0[q] = __ldg(pp);
-                    if (FP) st1[q] = __ldg(pp + 1);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int e = eb + b0 + q;
-                if (e < E0 || e >= E1) continue;
-                if (s_ptr[col + 1] <= e) {
-                    while (s_ptr[col + 1] <= e) { flush_acc(tc[col], acc); ++col; }
-                    c = cls_of(tc[col].c);
-                }
-                if (FP) {
-                    const double a = dv[b0 + q];
-                    const double r = i4_double_lo(st0[q]), m1 = i4_double_lo(st1[q]), m2 = i4_double_hi(st1[q]);
-                    if (classify_fp(r, a, m1, m2, st0[q].z, c, acc)) exact_put(d, tc + col, true, 0, 0, r, a, m1, m2, st0[q].z);
-                    if (st0[q].w >= 0 && classify_fp(dflip(r), dflip(a), m2, m1, st0[q].w, c, acc))
-                        exact_put(d, tc + col, true, 0, 0, dflip(r), dflip(a), m2, m1, st0[q].w);
-                } else {
-                    const long long a = iv[b0 + q];
-                    const long long r = row_r(st0[q]);
-                    if (classify_int(r, a, st0[q].z, c, acc)) exact_put(d, tc + col, false, r, a, 0, 0, 0, 0, st0[q].z);
-                    if (st0[q].w >= 0 && classify_int(-r, -a, st0[q].w, c, acc))
-                        exact_put(d, tc + col, false, -r, -a, 0, 0, 0, 0, st0[q].w);
-                }
-            }
+        Half h;
+        h.type = 0;
+        exact_item(it, W.ctx[g], acc, h);
+        if (acc.beta) atomicAdd(reinterpret_cast<unsigned long long *>(&W.beta[g]), (unsigned long long)acc.beta);
+        if (acc.alpha) atomicAdd(reinterpret_cast<unsigned long long *>(&W.alpha[g]), (unsigned long long)acc.alpha);
+        if (acc.beta_c) atomicAdd(&W.beta_c[g], acc.beta_c);
+        if (acc.alpha_c) atomicAdd(&W.alpha_c[g], acc.alpha_c);
+        if (h.type != 0) {
+            const int pos = atomicAdd(&W.cnt[g], 1);
+            if (pos < kGrpStage)
+                W.stage[g * kGrpStage + pos] = SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
         }
-        flush_acc(tc[col], acc);
     }
+    __syncwarp();
 }
 
 // Candidate evaluation of one sorted entry (prefix sums P / Pc inclusive).
-__device__ __forceinline__ void eval_sorted(VCand &vb, const TileCol &t, unsigned long long kk, long long del,
-                                            unsigned aux, long long P, int Pc, unsigned long long kprev, bool has_prev,
-                                            unsigned long long knext, unsigned anext, long long nviol, long long bestnv)
+__device__ __forceinline__ void eval_entry(VCand &vb, const ColCtx &c, const Acc &a, unsigned long long kk,
+                                           long long del, unsigned aux, long long P, int Pc, unsigned long long kprev,
+                                           bool has_prev, unsigned long long knext, unsigned anext, long long nviol,
+                                           long long bestnv)
 {
     if (!is_candidate(kk, aux, kprev, has_prev, knext, anext)) return;
     const bool post = aux_post(aux) != 0;
     const long long Pi = P - (post ? del : 0);
     const int Pci = Pc - (post ? aux_dc(aux) : 0);
-    const bool right = kk > t.c.kxb;
-    consider(vb, t.c, kk, t.beta + Pi + (right ? t.alpha : 0), t.beta_c + Pci + (right ? t.alpha_c : 0), nviol, bestnv);
+    const bool right = kk > c.kxb;
+    consider(vb, c, kk, a.beta + Pi + (right ? a.alpha : 0), a.beta_c + Pci + (right ? a.alpha_c : 0), nviol, bestnv);
 }
 
-template <int K>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long long (&del)[K], unsigned (&aux)[K],
-                                             int lane)
+__device__ __forceinline__ void load_entry(const SEnt *p, unsigned long long &key, long long &del, unsigned &aux)
 {
-    constexpr int N = 32 * K;
+    const int4 raw = *reinterpret_cast<const int4 *>(p);
+    key = ((unsigned long long)(unsigned)raw.y << 32) | (unsigned)raw.x;
+    del = raw.z;
+    aux = (unsigned)raw.w;
+}
+
+// Bitonic sort of G * K entries held K per lane by aligned groups of G lanes
+// (entry index sub * K + k, sub = lane % G).
+template <int K, int G>
+__device__ __forceinline__ void group_bitonic(unsigned long long (&key)[K], long long (&del)[K], unsigned (&aux)[K],
+                                              int sub)
+{
+    constexpr int N = G * K;
 #pragma unroll
     for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
@@ -971,7 +886,7 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long 
                 for (int k = 0; k < K; ++k) {
                     if ((k & stride) == 0) {
                         const int k2 = k | stride;
-                        const int i = lane * K + k;
+                        const int i = sub * K + k;
                         const bool asc = (i & size) == 0;
                         if (entry_less(key[k2], aux[k2], key[k], aux[k]) == asc) {
                             unsigned long long tk = key[k]; key[k] = key[k2]; key[k2] = tk;
@@ -984,13 +899,14 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long 
                 const int ls = stride / K;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    unsigned long long pk = __shfl_xor_sync(FULLMASK, key[k], ls);
-                    long long pd = __shfl_xor_sync(FULLMASK, del[k], ls);
-                    unsigned pa = __shfl_xor_sync(FULLMASK, aux[k], ls);
-                    const int i = lane * K + k;
+                    const unsigned long long pk = __shfl_xor_sync(FULLMASK, key[k], ls);
+                    const long long pd = __shfl_xor_sync(FULLMASK, del[k], ls);
+                    const unsigned pa = __shfl_xor_sync(FULLMASK, aux[k], ls);
+                    const int i = sub * K + k;
                     const bool lower = (i & stride) == 0;
                     const bool asc = (i & size) == 0;
-                    bool take = (lower == asc) ? entry_less(pk, pa, key[k], aux[k]) : entry_less(key[k], aux[k], pk, pa);
+                    const bool take = (lower == asc) ? entry_less(pk, pa, key[k], aux[k])
+                                                     : entry_less(key[k], aux[k], pk, pa);
                     if (take) { key[k] = pk; del[k] = pd; aux[k] = pa; }
                 }
             }
@@ -998,27 +914,23 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[K], long 
     }
 }
 
-// One column per warp, K entries per lane (segments of up to 32K entries).
-template <int K>
-__device__ void warp_sort(const Dev &d, const VarOut &o, const TileCol &t, const SEnt *pool, long long nviol,
-                          long long bestnv, Cand &best)
+// Sort, scan and argmax of each group's list (cnt <= G * K entries at list),
+// K entries per lane; every lane returns the best candidate of its group.
+template <int K, int G>
+__device__ __forceinline__ VCand group_sort_scan(const ColCtx &c, const Acc &a, const SEnt *list, int cnt,
+                                                 long long nviol, long long bestnv)
 {
-    const int lane = threadIdx.x & 31;
+    const int sub = (threadIdx.x & 31) & (G - 1);
     unsigned long long key[K];
     long long del[K];
     unsigned aux[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int idx = lane * K + k;
-        if (idx < t.cnt) {
-            const int4 raw = __ldcg(reinterpret_cast<const int4 *>(pool + idx));
-            key[k] = ((unsigned long long)(unsigned)raw.y << 32) | (unsigned)raw.x;
-            del[k] = raw.z;
-            aux[k] = (unsigned)raw.w;
-        }
+        const int idx = sub * K + k;
+        if (idx < cnt) load_entry(list + idx, key[k], del[k], aux[k]);
         else { key[k] = kPadKey; del[k] = 0; aux[k] = make_aux(1, 0); }
     }
-    warp_bitonic<K>(key, del, aux, lane);
+    group_bitonic<K, G>(key, del, aux, sub);
     long long P[K];
     int Pc[K];
     long long run = 0;
@@ -1028,294 +940,260 @@ __device__ void warp_sort(const Dev &d, const VarOut &o, const TileCol &t, const
     long long tot = run;
     int totc = runc;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const long long x = __shfl_up_sync(FULLMASK, tot, off);
-        const int y = __shfl_up_sync(FULLMASK, totc, off);
-        if (lane >= off) { tot += x; totc += y; }
+    for (int off = 1; off < G; off <<= 1) {
+        const long long x = __shfl_up_sync(FULLMASK, tot, off, G);
+        const int y = __shfl_up_sync(FULLMASK, totc, off, G);
+        if (sub >= off) { tot += x; totc += y; }
     }
     const long long ex = tot - run;
     const int exc = totc - runc;
-    unsigned long long nk = __shfl_down_sync(FULLMASK, key[0], 1);
-    unsigned na = __shfl_down_sync(FULLMASK, aux[0], 1);
-    const unsigned long long pk = __shfl_up_sync(FULLMASK, key[K - 1], 1);
-    if (lane == 31) { nk = kPadKey; na = make_aux(1, 0); }
+    unsigned long long nk = __shfl_down_sync(FULLMASK, key[0], 1, G);
+    unsigned na = __shfl_down_sync(FULLMASK, aux[0], 1, G);
+    const unsigned long long pk = __shfl_up_sync(FULLMASK, key[K - 1], 1, G);
+    if (sub == G - 1) { nk = kPadKey; na = make_aux(1, 0); }
     VCand vb{0, 0ull, 0, 0};
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const unsigned long long knext = (k + 1 < K) ? key[(k + 1) % K] : nk;
         const unsigned anext = (k + 1 < K) ? aux[(k + 1) % K] : na;
         const unsigned long long kprev = (k > 0) ? key[(k + K - 1) % K] : pk;
-        eval_sorted(vb, t, key[k], del[k], aux[k], ex + P[k], exc + Pc[k], kprev, k > 0 || lane > 0, knext, anext,
-                    nviol, bestnv);
+        eval_entry(vb, c, a, key[k], del[k], aux[k], ex + P[k], exc + Pc[k], kprev, k > 0 || sub > 0, knext, anext,
+                   nviol, bestnv);
     }
-    warp_reduce_vc(vb, t.c);
-    if (lane == 0) finish_column(d, o, t.c, vb, best);
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        VCand p;
+        p.s = __shfl_xor_sync(FULLMASK, vb.s, o);
+        p.key = __shfl_xor_sync(FULLMASK, vb.key, o);
+        p.dc = __shfl_xor_sync(FULLMASK, vb.dc, o);
+        p.valid = __shfl_xor_sync(FULLMASK, vb.valid, o);
+        if (vc_better(p, vb, c)) vb = p;
+    }
+    return vb;
 }
 
-// Sort, scan and argmax of one column's entries staged in shared memory, on
-// S lanes of the warp (one entry per lane, S = 8, 16 or 32).
-template <int S>
-__device__ void lane_sort(const Dev &d, const VarOut &o, const TileCol &t, const SEnt *ent, long long nviol,
-                          long long bestnv, Cand &best)
+// Whole-warp evaluation of one column with up to kWarpSortMax list entries
+// (columns whose list outgrew the group path).  Exact breakpoints inline.
+__device__ __noinline__ void column_warp(const Dev &d, const VarOut &o, int q, SEnt *stage, long long iter,
+                                         long long nviol, long long bestnv, Cand &best)
 {
     const int lane = threadIdx.x & 31;
-    const int sub = lane & (S - 1);
-    const bool own = lane < S;
-    unsigned long long key = kPadKey;
-    long long del = 0;
-    unsigned aux = make_aux(1, 0);
-    if (own && sub < t.cnt) {
-        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(ent + sub));
-        key = ((unsigned long long)(unsigned)raw.y << 32) | (unsigned)raw.x;
-        del = raw.z;
-        aux = (unsigned)raw.w;
+    const ColCtx c = make_col(d, q, iter);
+    const int nv = c.nI + c.nF;
+    int cnt;
+    {
+        const bool fl = isfinite(__ldg(d.lb + c.j)), fu = isfinite(__ldg(d.ub + c.j));
+        if (lane == 0) {
+            if (fl) stage[0] = SEnt{c.kl, 0, make_aux(0, 0)};
+            if (fu) stage[fl ? 1 : 0] = SEnt{c.ku, 0, make_aux(0, 0)};
+        }
+        cnt = (int)fl + (int)fu;
     }
+    Acc acc{0, 0, 0, 0};
+    for (int v = lane; v - lane < nv; v += 32) {
+        Half h1, h2;
+        h1.type = 0;
+        h2.type = 0;
+        if (v < nv) gen_entry(d, c, v, acc, h1, h2);
 #pragma unroll
-    for (int size = 2; size <= S; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const unsigned long long pk = __shfl_xor_sync(FULLMASK, key, stride);
-            const long long pd = __shfl_xor_sync(FULLMASK, del, stride);
-            const unsigned pa = __shfl_xor_sync(FULLMASK, aux, stride);
-            const bool lower = (sub & stride) == 0;
-            const bool asc = (sub & size) == 0;
-            const bool take = (lower == asc) ? entry_less(pk, pa, key, aux) : entry_less(key, aux, pk, pa);
-            if (take) { key = pk; del = pd; aux = pa; }
+        for (int hh = 0; hh < 2; ++hh) {
+            const Half &h = hh ? h2 : h1;
+            const bool has = h.type != 0;
+            const unsigned bal = __ballot_sync(FULLMASK, has);
+            if (has)
+                stage[cnt + __popc(bal & ((1u << lane) - 1u))] =
+                    SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
+            cnt += __popc(bal);
         }
     }
-    long long P = del;
-    int Pc = aux_dc(aux);
-#pragma unroll
-    for (int off = 1; off < S; off <<= 1) {
-        const long long x = __shfl_up_sync(FULLMASK, P, off, S);
-        const int y = __shfl_up_sync(FULLMASK, Pc, off, S);
-        if (sub >= off) { P += x; Pc += y; }
-    }
-    unsigned long long knext = __shfl_down_sync(FULLMASK, key, 1, S);
-    unsigned anext = __shfl_down_sync(FULLMASK, aux, 1, S);
-    const unsigned long long kprev = __shfl_up_sync(FULLMASK, key, 1, S);
-    if (sub == S - 1) { knext = kPadKey; anext = make_aux(1, 0); }
-    VCand vb{0, 0ull, 0, 0};
-    if (own) eval_sorted(vb, t, key, del, aux, P, Pc, kprev, sub > 0, knext, anext, nviol, bestnv);
-    warp_reduce_vc(vb, t.c);
-    if (lane == 0) finish_column(d, o, t.c, vb, best);
+    warp_allreduce_acc(acc);
+    __syncwarp();
+    VCand vb;
+    if (cnt <= 32) vb = group_sort_scan<1, 32>(c, acc, stage, cnt, nviol, bestnv);
+    else if (cnt <= 64) vb = group_sort_scan<2, 32>(c, acc, stage, cnt, nviol, bestnv);
+    else vb = group_sort_scan<4, 32>(c, acc, stage, cnt, nviol, bestnv);
+    if (lane == 0) finish_column(d, o, c, vb, best);
+    __syncwarp();
 }
 
-// Short non-binary columns (at most kWarpSortMax breakpoint entries): a tile of
-// up to kNbTileCols consecutive columns per CTA, three converged phases.
-//  1. The tile's nonzeros are streamed in aligned groups of 8 per thread (as in
-//     the binary pass); every half is classified by products: its Algorithm 1
-//     scalars are accumulated, and the few halves whose breakpoint may lie in
-//     [l, u] are appended to a shared-memory queue.
-//  2. The queued halves (compacted: all lanes busy) get their exact breakpoint;
-//     entries inside [l, u] go to the column's list in the scratch.
-//  3. One thread per column: insertion sort of its short list by (t, marker)
-//     (a segmented sort with one segment per thread), scan, argmax.
-struct NbShared {
-    ColCtx ctx[kNbTileCols];
-    long long beta[kNbTileCols], alpha[kNbTileCols];
-    int beta_c[kNbTileCols], alpha_c[kNbTileCols], cnt[kNbTileCols];
-    int pi[kNbTileCols + 1], pf[kNbTileCols + 1];
-    int qn;
-};
-
-__device__ __forceinline__ void nb_flush(NbShared &S, int col, Acc &a)
-{
-    if (a.beta) atomicAdd(reinterpret_cast<unsigned long long *>(&S.beta[col]), (unsigned long long)a.beta);
-    if (a.alpha) atomicAdd(reinterpret_cast<unsigned long long *>(&S.alpha[col]), (unsigned long long)a.alpha);
-    if (a.beta_c) atomicAdd(&S.beta_c[col], a.beta_c);
-    if (a.alpha_c) atomicAdd(&S.alpha_c[col], a.alpha_c);
-    a = Acc{0, 0, 0, 0};
-}
-
-// queue item: nonzero index inside the part, column, part (1 = non-integral rows), half
-__device__ __forceinline__ unsigned nb_item(int el, int col, int part, int half)
-{
-    return ((unsigned)el << 10) | ((unsigned)col << 2) | ((unsigned)part << 1) | (unsigned)half;
-}
-
-template <bool FP>
-__device__ __forceinline__ void nb_stream(const Dev &d, NbShared &S, int nc, unsigned *queue)
-{
-    const int *s_ptr = FP ? S.pf : S.pi;
-    const int E0 = s_ptr[0], E1 = s_ptr[nc];
-    const int g1 = (E1 + 7) >> 3;
-    for (int g = (E0 >> 3) + threadIdx.x; g < g1; g += blockDim.x) {
-        const int eb = g << 3;
-        int rows[8];
-        {
-            const int4 *rp = reinterpret_cast<const int4 *>((FP ? d.cf_row : d.ci_row) + eb);
-            const int4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-            rows[0] = r0.x; rows[1] = r0.y; rows[2] = r0.z; rows[3] = r0.w;
-            rows[4] = r1.x; rows[5] = r1.y; rows[6] = r1.z; rows[7] = r1.w;
-        }
-        double dv[8];
-        int iv[8];
-        if (FP) {
-            const double2 *vp = reinterpret_cast<const double2 *>(d.cf_val + eb);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { const double2 v = __ldg(vp + k); dv[2 * k] = v.x; dv[2 * k + 1] = v.y; }
-        } else {
-            const int4 *vp = reinterpret_cast<const int4 *>(d.ci_val + eb);
-            const int4 v0 = __ldg(vp), v1 = __ldg(vp + 1);
-            iv[0] = v0.x; iv[1] = v0.y; iv[2] = v0.z; iv[3] = v0.w;
-            iv[4] = v1.x; iv[5] = v1.y; iv[6] = v1.z; iv[7] = v1.w;
-        }
-        int col = find_col(s_ptr, nc, max(eb, E0));
-        ClsCtx c = cls_of(S.ctx[col]);
-        Acc acc{0, 0, 0, 0};
-        constexpr int B = FP ? 4 : 8;
-#pragma unroll
-        for (int b0 = 0; b0 < 8; b0 += B) {
-            int4 st0[B], st1[B];
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int e = eb + b0 + q;
-                if (e >= E0 && e < E1) {
-                    const int4 *pp = reinterpret_cast<const int4 *>(d.rs + rows[b0 + q]);
-                    st0[q] = __ldg(pp);
-                    if (FP) st1[q] = __ldg(pp + 1);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int e = eb + b0 + q;
-                if (e < E0 || e >= E1) continue;
-                if (s_ptr[col + 1] <= e) {
-                    while (s_ptr[col + 1] <= e) { nb_flush(S, col, acc); ++col; }
-                    c = cls_of(S.ctx[col]);
-                }
-                bool q1, q2 = false;
-                if (FP) {
-                    const double a = dv[b0 + q];
-                    const double r = i4_double_lo(st0[q]), m1 = i4_double_lo(st1[q]), m2 = i4_double_hi(st1[q]);
-                    q1 = classify_fp(r, a, m1, m2, st0[q].z, c, acc);
-                    if (st0[q].w >= 0) q2 = classify_fp(dflip(r), dflip(a), m2, m1, st0[q].w, c, acc);
-                } else {
-                    const long long a = iv[b0 + q];
-                    const long long r = row_r(st0[q]);
-                    q1 = classify_int(r, a, st0[q].z, c, acc);
-                    if (st0[q].w >= 0) q2 = classify_int(-r, -a, st0[q].w, c, acc);
-                }
-                if (q1 | q2) {
-                    int pos = atomicAdd(&S.qn, (int)q1 + (int)q2);
-                    if (q1) queue[pos++] = nb_item(e - E0, col, FP ? 1 : 0, 0);
-                    if (q2) queue[pos] = nb_item(e - E0, col, FP ? 1 : 0, 1);
-                }
-            }
-        }
-        nb_flush(S, col, acc);
-    }
-}
-
-__global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, const Tile *tiles, VarOut o, int slot0, int gate)
+__global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int ncols, VarOut o, int slot0, int gate)
 {
     if (gated_done(d, gate)) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    unsigned *queue = reinterpret_cast<unsigned *>(smem);
-    __shared__ NbShared S;
-    const Tile tl = tiles[blockIdx.x];
+    extern __shared__ __align__(16) unsigned char nb_smem[];
+    NbWarp *warps = reinterpret_cast<NbWarp *>(nb_smem);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / kGrp, sub = lane & (kGrp - 1);
+    NbWarp &W = warps[warp];
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
-    const int nc = tl.end - tl.begin;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int q = tl.begin + c;
-        const ColCtx cc = make_col(d, q, iter);
-        S.ctx[c] = cc;
-        S.beta[c] = 0; S.alpha[c] = 0; S.beta_c[c] = 0; S.alpha_c[c] = 0;
-        SEnt *list = d.lists + __ldg(d.list_off + (q - d.nb_pos0));
-        const double l = __ldg(d.lb + cc.j), u = __ldg(d.ub + cc.j);
-        int n = 0;
-        if (isfinite(l)) list[n++] = SEnt{cc.kl, 0, make_aux(0, 0)};
-        if (isfinite(u)) list[n++] = SEnt{cc.ku, 0, make_aux(0, 0)};
-        S.cnt[c] = n;
-    }
-    for (int c = threadIdx.x; c <= nc; c += blockDim.x) {
-        S.pi[c] = __ldg(d.ci_ptr + tl.begin + c);
-        S.pf[c] = __ldg(d.cf_ptr + tl.begin + c);
-    }
-    if (threadIdx.x == 0) S.qn = 0;
-    __syncthreads();
-    nb_stream<false>(d, S, nc, queue);
-    nb_stream<true>(d, S, nc, queue);
-    __syncthreads();
-    // phase 2: exact breakpoints of the queued halves
-    const int qn = S.qn;
-    for (int k = threadIdx.x; k < qn; k += blockDim.x) {
-        const unsigned it = queue[k];
-        const int half = it & 1, part = (it >> 1) & 1, col = (it >> 2) & 255, el = (int)(it >> 10);
-        const ColCtx &c = S.ctx[col];
-        Acc acc{0, 0, 0, 0};
-        Half h;
-        h.type = 0;
-        if (part == 0) {
-            const int e = S.pi[0] + el;
-            const int4 st = ld_row16(d.rs + __ldg(d.ci_row + e));
-            const long long a = __ldg(d.ci_val + e);
-            const long long r = row_r(st);
-            if (half == 0) int_half_exact(r, a, st.z, c, acc, h);
-            else int_half_exact(-r, -a, st.w, c, acc, h);
-        } else {
-            const int e = S.pf[0] + el;
-            const int4 *p = reinterpret_cast<const int4 *>(d.rs + __ldg(d.cf_row + e));
-            const double a = __ldg(d.cf_val + e);
-            const int4 s0 = __ldg(p), s1 = __ldg(p + 1);
-            const double r = i4_double_lo(s0), m1 = i4_double_lo(s1), m2 = i4_double_hi(s1);
-            if (half == 0) fp_half_exact(r, a, m1, m2, s0.z, c, acc, h);
-            else fp_half_exact(dflip(r), dflip(a), m2, m1, s0.w, c, acc, h);
-        }
-        nb_flush(S, col, acc);
-        if (h.type != 0) {
-            SEnt *list = d.lists + __ldg(d.list_off + (tl.begin + col - d.nb_pos0));
-            list[atomicAdd(&S.cnt[col], 1)] = SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
-        }
-    }
-    __syncthreads();
-    // phase 3: one thread per column
     Cand best{0, kNoVar, 0, 0.0};
-    for (int cidx = threadIdx.x; cidx < nc; cidx += blockDim.x) {
-        const ColCtx &c = S.ctx[cidx];
-        SEnt *list = d.lists + __ldg(d.list_off + (tl.begin + cidx - d.nb_pos0));
-        const int cnt = S.cnt[cidx];
-        for (int i = 1; i < cnt; ++i) {
-            const int4 ri = __ldcg(reinterpret_cast<const int4 *>(list + i));
-            const unsigned long long ek = ((unsigned long long)(unsigned)ri.y << 32) | (unsigned)ri.x;
-            const unsigned ea = (unsigned)ri.w;
-            int j = i - 1;
-            while (j >= 0) {
-                const int4 rj = __ldcg(reinterpret_cast<const int4 *>(list + j));
-                const unsigned long long jk = ((unsigned long long)(unsigned)rj.y << 32) | (unsigned)rj.x;
-                if (!entry_less(ek, ea, jk, (unsigned)rj.w)) break;
-                *reinterpret_cast<int4 *>(list + j + 1) = rj;
-                --j;
+    const int nquad = (ncols + kGrpPerWarp - 1) / kGrpPerWarp;
+    for (int qd = blockIdx.x * kNbWarps + warp; qd < nquad; qd += gridDim.x * kNbWarps) {
+        const int cq = qd * kGrpPerWarp + g;
+        const bool live = cq < ncols;
+        int nI, nv, ci0, cf0;
+        float Lp, Ln, Up, Un, tolf;
+        bool fok, isint;
+        {
+            const ColCtx c = make_col(d, q0 + (live ? cq : 0), iter);
+            nI = live ? c.nI : 0;
+            nv = live ? c.nI + c.nF : 0;
+            ci0 = c.ci0;
+            cf0 = c.cf0;
+            isint = c.isint;
+            fok = c.fok;
+            // thresholds of the side test (z / a against L, U with a > 0):
+            // integer variable (z = eps - r): t < l <=> z/a < lo (a > 0) or
+            // z/a <= lo - 1 (a < 0); t > u <=> z/a >= hi + 1 (a > 0) or z/a > hi
+            // (a < 0).  Continuous (z = -r): t < l <=> z/a < l - xbar,
+            // t > u <=> z/a > u - xbar, with a margin for the rounding of t.
+            Lp = isint ? c.lof : -c.dlf;
+            Ln = isint ? c.lof - 1.0f : -c.dlf;
+            Up = isint ? c.hif + 1.0f : -c.duf;
+            Un = isint ? c.hif : -c.duf;
+            tolf = c.xaf * 1.0e-10f;
+            if (sub == 0) {
+                W.ctx[g] = c;
+                W.beta[g] = 0; W.alpha[g] = 0; W.beta_c[g] = 0; W.alpha_c[g] = 0;
+                int n = 0;
+                if (live) {
+                    if (isfinite(__ldg(d.lb + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.kl, 0, make_aux(0, 0)};
+                    if (isfinite(__ldg(d.ub + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.ku, 0, make_aux(0, 0)};
+                }
+                W.cnt[g] = n;
             }
-            *reinterpret_cast<int4 *>(list + j + 1) = ri;
         }
-        const long long beta = S.beta[cidx], alpha = S.alpha[cidx];
-        const int bc = S.beta_c[cidx], ac = S.alpha_c[cidx];
-        long long P = 0;
-        int Pc = 0;
-        VCand vb{0, 0ull, 0, 0};
-        unsigned long long kprev = 0ull;
-        int4 cur = cnt > 0 ? __ldcg(reinterpret_cast<const int4 *>(list)) : make_int4(0, 0, 0, 0);
-        for (int i = 0; i < cnt; ++i) {
-            const int4 nxt = i + 1 < cnt ? __ldcg(reinterpret_cast<const int4 *>(list + i + 1)) : make_int4(-1, -1, 0, (int)make_aux(1, 0));
-            const unsigned long long ek = ((unsigned long long)(unsigned)cur.y << 32) | (unsigned)cur.x;
-            const unsigned ea = (unsigned)cur.w;
-            const long long del = cur.z;
-            P += del;
-            Pc += aux_dc(ea);
-            const unsigned long long knext = ((unsigned long long)(unsigned)nxt.y << 32) | (unsigned)nxt.x;
-            if (is_candidate(ek, ea, kprev, i > 0, knext, (unsigned)nxt.w)) {
-                const bool post = aux_post(ea) != 0;
-                const long long Pi = P - (post ? del : 0);
-                const int Pci = Pc - (post ? aux_dc(ea) : 0);
-                const bool right = ek > c.kxb;
-                consider(vb, c, ek, beta + Pi + (right ? alpha : 0), bc + Pci + (right ? ac : 0), nviol, bestnv);
+        __syncwarp();
+        int head = 0, qn = 0;
+        Acc acc{0, 0, 0, 0};
+        int nvmax = nv;
+#pragma unroll
+        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) nvmax = max(nvmax, __shfl_xor_sync(FULLMASK, nvmax, o2));
+        for (int base = 0; base < nvmax; base += 2 * kGrp) {
+            int row[2];
+            long long ai[2];
+            double ad[2];
+            bool ok[2], fp[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int v = base + k * kGrp + sub;
+                ok[k] = v < nv;
+                fp[k] = v >= nI;
+                row[k] = 0;
+                ai[k] = 0;
+                ad[k] = 0.0;
+                if (ok[k]) {
+                    if (fp[k]) {
+                        const int e = cf0 + (v - nI);
+                        row[k] = __ldg(d.cf_row + e);
+                        ad[k] = __ldg(d.cf_val + e);
+                    } else {
+                        const int e = ci0 + v;
+                        row[k] = __ldg(d.ci_row + e);
+                        ai[k] = __ldg(d.ci_val + e);
+                    }
+                }
             }
-            kprev = ek;
-            cur = nxt;
+            int4 s0[2], s1[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                s0[k] = make_int4(0, 0, 0, -1);
+                s1[k] = make_int4(0, 0, 0, 0);
+                if (ok[k]) {
+                    const int4 *p = reinterpret_cast<const int4 *>(d.rs + row[k]);
+                    s0[k] = __ldg(p);
+                    if (fp[k]) s1[k] = __ldg(p + 1);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    const int w = hf ? s0[k].w : s0[k].z;
+                    const bool act = ok[k] && (hf == 0 || s0[k].w >= 0);
+                    bool viol, apos, tight0 = false, fin = true;
+                    float zf, af;
+                    long long qx, qa;
+                    if (!fp[k]) {
+                        const long long r = hf ? -row_r(s0[k]) : row_r(s0[k]);
+                        const long long a = hf ? -ai[k] : ai[k];
+                        viol = r > 0;
+                        apos = a > 0;
+                        zf = ll_approx(-r);
+                        af = (float)a;
+                        qx = r;
+                        qa = a;
+                    } else {
+                        const double r0 = i4_double_lo(s0[k]);
+                        const double r = hf ? dflip(r0) : r0, a = hf ? dflip(ad[k]) : ad[k];
+                        const double m = hf ? i4_double_hi(s1[k]) : i4_double_lo(s1[k]);
+                        const double mo = hf ? i4_double_lo(s1[k]) : i4_double_hi(s1[k]);
+                        viol = dneg(m);
+                        apos = !dneg(a);
+                        tight0 = !isint && !viol && !dneg(mo);  // |r| <= eps: tight wherever t is
+                        fin = fok;
+                        zf = approx_f(isint ? m : dflip(r), fin);
+                        af = approx_f(a, fin);
+                        qx = __double_as_longlong(isint ? m : r);
+                        qa = __double_as_longlong(a);
+                    }
+                    int side = 0;
+                    if (fin) {
+                        if (!apos) { zf = -zf; af = -af; }
+                        side = side_of(zf, af, apos ? Lp : Ln, apos ? Up : Un, tolf * af);
+                    }
+                    if (act && (tight0 || side != 0)) half_acc(viol, tight0, apos, side, w, acc);
+                    const bool pend = act && !tight0 && side == 0;
+                    const unsigned bal = __ballot_sync(FULLMASK, pend);
+                    if (pend) {
+                        int pos = head + qn + __popc(bal & ((1u << lane) - 1u));
+                        if (pos >= kQCap) pos -= kQCap;
+                        W.q[pos] = QItem{qx, qa, w, g | ((int)fp[k] << 2) | ((int)viol << 3)};
+                    }
+                    qn += __popc(bal);
+                }
+            }
+            __syncwarp();
+            while (qn >= 32) {
+                flush_queue(W, head, 32, lane);
+                head += 32;
+                if (head >= kQCap) head -= kQCap;
+                qn -= 32;
+            }
         }
-        finish_column(d, o, c, vb, best);
+        if (qn > 0) flush_queue(W, head, qn, lane);
+        // group sums of the scalars
+#pragma unroll
+        for (int o2 = kGrp >> 1; o2 > 0; o2 >>= 1) {
+            acc.beta += __shfl_xor_sync(FULLMASK, acc.beta, o2);
+            acc.alpha += __shfl_xor_sync(FULLMASK, acc.alpha, o2);
+            acc.beta_c += __shfl_xor_sync(FULLMASK, acc.beta_c, o2);
+            acc.alpha_c += __shfl_xor_sync(FULLMASK, acc.alpha_c, o2);
+        }
+        acc.beta += W.beta[g];
+        acc.alpha += W.alpha[g];
+        acc.beta_c += W.beta_c[g];
+        acc.alpha_c += W.alpha_c[g];
+        const int cnt = W.cnt[g];
+        const bool over = cnt > kGrpStage;
+        int cmax = over ? 0 : cnt;
+#pragma unroll
+        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) cmax = max(cmax, __shfl_xor_sync(FULLMASK, cmax, o2));
+        {
+            const ColCtx &c = W.ctx[g];
+            const SEnt *list = W.stage + g * kGrpStage;
+            VCand vb;
+            if (cmax <= kGrp) vb = group_sort_scan<1, kGrp>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
+            else if (cmax <= 2 * kGrp) vb = group_sort_scan<2, kGrp>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
+            else vb = group_sort_scan<4, kGrp>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
+            if (sub == 0 && live && !over) finish_column(d, o, c, vb, best);
+        }
+        __syncwarp();
+        unsigned ovf = __ballot_sync(FULLMASK, sub == 0 && live && over);
+        while (ovf) {
+            const int gg = (__ffs(ovf) - 1) / kGrp;
+            ovf &= ovf - 1;
+            column_warp(d, o, q0 + qd * kGrpPerWarp + gg, W.stage, iter, nviol, bestnv, best);
+        }
     }
     const Cand bb = block_reduce_cand(best);
     if (threadIdx.x == 0) d.block_best[slot0 + blockIdx.x] = bb;
@@ -1816,10 +1694,30 @@ static int grid_for(long long n, int threads, int cap = 152 * 8)
     return (int)g;
 }
 
+int nb_grid_size(int ncols)
+{
+    // one resident wave: every SM holds as many CTAs as fit, and no CTA is
+    // launched without a column for each of its warps to start with
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(k_eval_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, kNbSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_nb, kEvalThreads, kNbSmem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    const long long need = ((long long)ncols + kNbWarps - 1) / kNbWarps;
+    const long long cap = (long long)sms * per_sm;
+    return (int)(need < cap ? need : cap);
+}
+
 cudaError_t setup_kernel_attributes(const LaunchPlan &p)
 {
     cudaError_t e = cudaSuccess;
-    if (p.nb_smem > 0) e = cudaFuncSetAttribute(k_eval_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, p.nb_smem);
+    if (p.nb_grid > 0) e = cudaFuncSetAttribute(k_eval_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, kNbSmem);
     if (e == cudaSuccess && p.cta_smem > 0)
         e = cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, p.cta_smem);
     if (e == cudaSuccess && p.hist_smem > 0)
@@ -1834,12 +1732,12 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     // selection.  The same fork/join shape is recorded by graph capture.
     if (o.xhat || o.s || o.dc) k_fill_outputs<<<grid_for(d.n, 256), 256, 0, st>>>(d, o);
     cudaError_t e = cudaEventRecord(p.ev_fork, st);
-    const bool side[3] = {p.n_nb > 0, p.n_cta > 0, p.n_hist_tiles > 0};
+    const bool side[3] = {p.nb_grid > 0, p.n_cta > 0, p.n_hist_tiles > 0};
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (side[k]) e = cudaStreamWaitEvent(p.side[k], p.ev_fork, 0);
     if (e != cudaSuccess) return e;
     if (p.n_bin) k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.tiles_bin, o, gate);
-    if (p.n_nb) k_eval_nb<<<p.n_nb, kEvalThreads, p.nb_smem, p.side[0]>>>(d, p.tiles_nb, o, p.slot_nb, gate);
+    if (p.nb_grid) k_eval_nb<<<p.nb_grid, kEvalThreads, kNbSmem, p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
     if (p.n_cta) k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
     if (p.n_hist_tiles) k_eval_hist<<<p.n_hist_tiles, kHistThreads, p.hist_smem, p.side[2]>>>(d, p.tiles_hist, o, gate);
     e = cudaGetLastError();
