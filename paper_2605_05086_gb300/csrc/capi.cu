@@ -363,11 +363,21 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         kind_vars[k].push_back(j);
     }
     {
-        // short columns (one warp each, strided over the grid): order them by
-        // entry count so that the CTAs of one wave get similar mixes
+        // binary columns (four to a warp): order them by length
+        std::vector<int> &bv = kind_vars[T_BIN];
+        std::stable_sort(bv.begin(), bv.end(), [&](int x, int y) {
+            return p->col_ptr[x + 1] - p->col_ptr[x] < p->col_ptr[y + 1] - p->col_ptr[y];
+        });
+    }
+    {
+        // short columns (four to a warp): order them by type, then entry count,
+        // so that the columns of one warp have similar lengths and row mixes
         std::vector<int> ord(nb_cap.size());
         for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
-        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return nb_cap[x] < nb_cap[y]; });
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+            const int tx = h->vtype[kind_vars[T_NB][x]], ty = h->vtype[kind_vars[T_NB][y]];
+            return tx != ty ? tx < ty : nb_cap[x] < nb_cap[y];
+        });
         std::vector<int> vs(ord.size()), cs(ord.size());
         for (size_t q = 0; q < ord.size(); ++q) { vs[q] = kind_vars[T_NB][ord[q]]; cs[q] = nb_cap[ord[q]]; }
         kind_vars[T_NB].swap(vs);
@@ -407,26 +417,10 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
 
     // ---- work tiles
-    std::vector<Tile> tiles_bin, tiles_cta, tiles_hist;
+    std::vector<Tile> tiles_cta, tiles_hist;
     std::vector<HistCol> hcols;
     int max_cta_n = 0, max_hist_d = 0;
     int64_t hist_bins = 0;
-    {
-        // binary: consecutive columns up to ~kBinTileEntries nonzeros and kBinMaxCols columns
-        const int q0 = kind_base[T_BIN], q1 = kind_base[T_BIN + 1];
-        int start = q0;
-        int64_t ent = 0;
-        for (int q = q0; q < q1; ++q) {
-            const int64_t len = (int64_t)(ci_ptr[q + 1] - ci_ptr[q]) + (cf_ptr[q + 1] - cf_ptr[q]);
-            if (q > start && (ent + len > kBinTileEntries || q - start >= kBinMaxCols)) {
-                tiles_bin.push_back(Tile{T_BIN, start, q, 0});
-                start = q;
-                ent = 0;
-            }
-            ent += len;
-        }
-        if (q1 > start) tiles_bin.push_back(Tile{T_BIN, start, q1, 0});
-    }
     for (int k = T_NB; k < T_NUM_KINDS; ++k) {
         const int base = kind_base[k], cnt = kind_base[k + 1] - base;
         if (cnt == 0) continue;
@@ -457,7 +451,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
     const int nb_cols = kind_base[T_NB + 1] - kind_base[T_NB];
     const int n_tn = nb_cols > 0 ? nb_grid_size(nb_cols) : 0;
-    const int n_tb = (int)tiles_bin.size(), n_tc = (int)tiles_cta.size();
+    const int bin_cols = kind_base[T_BIN + 1] - kind_base[T_BIN];
+    const int n_tb = bin_cols > 0 ? bin_grid_size(bin_cols) : 0, n_tc = (int)tiles_cta.size();
     const int slot_hist = n_tb + n_tn + n_tc;
     for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = slot_hist + (int)q;
     const int n_bb = slot_hist + (int)hcols.size();
@@ -489,7 +484,6 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     int *vpos_d = dalloc<int>(h, n);
     d.block_best = dalloc<Cand>(h, n_bb);
     d.n_block_best = n_bb;
-    Tile *tb_d = dalloc<Tile>(h, tiles_bin.size());
     Tile *tc_d = dalloc<Tile>(h, tiles_cta.size());
     Tile *th_d = dalloc<Tile>(h, tiles_hist.size());
     HistCol *hc_d = dalloc<HistCol>(h, hcols.size());
@@ -503,7 +497,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     h->t_tabu = dalloc<long long>(h, n);
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && row_ptr_d && col_idx_d &&
               row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.rs &&
-              d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tb_d && tc_d && th_d && hc_d &&
+              d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
               d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
     if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
@@ -534,7 +528,6 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     UP(rhs_d, rhs.data(), m); UP(eps_d, eps.data(), m); UP(rint_d, rint.data(), m); UP(nrb_d, h->nrow_base.data(), m);
     UP(vt_d, p->vtype, n); UP(lb_d, p->lb, n); UP(ub_d, p->ub, n); UP(obj_d, h->obj.data(), n);
     UP(vl_d, var_list.data(), var_list.size()); UP(vpos_d, vpos.data(), n);
-    UP(tb_d, tiles_bin.data(), tiles_bin.size());
     UP(tc_d, tiles_cta.data(), tiles_cta.size());
     UP(th_d, tiles_hist.data(), tiles_hist.size()); UP(hc_d, hcols.data(), hcols.size());
 #undef UP
@@ -542,7 +535,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     if (e == cudaSuccess && !hcols.empty()) e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
     LaunchPlan &pl = h->plan;
-    pl.tiles_bin = tb_d; pl.n_bin = n_tb;
+    pl.bin_cols = bin_cols; pl.n_bin = n_tb;
     pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn;
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
     pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);

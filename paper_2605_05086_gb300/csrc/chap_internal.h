@@ -75,7 +75,7 @@ struct __align__(16) Ctl {
 
 // Work tiles of the best-shift pass.  A tile covers var_list[begin, end).
 enum TileKind : int {
-    T_BIN = 0,                // binary flips: consecutive columns streamed by one CTA
+    T_BIN = 0,                // binary flips: a group of lanes per column
     T_NB,                     // short breakpoint lists: one warp per column
     T_NB_CTA,                 // CTA bitonic sort in shared memory
     T_NB_HIST,                // multi-CTA counting sort (long integer columns)
@@ -168,8 +168,8 @@ struct VarOut {
 };
 
 struct LaunchPlan {
-    const Tile *tiles_bin;     // device
-    int n_bin;
+    int bin_cols;              // binary columns: positions [0, bin_cols)
+    int n_bin;                 // CTAs of the persistent binary kernel (0: no binary column)
     int nb_q0, nb_cols;        // positions of the short non-binary columns (<= kWarpSortMax entries)
     int nb_grid;               // CTAs of the persistent warp-per-column kernel (0: no such column)
     const Tile *tiles_cta;
@@ -187,7 +187,8 @@ struct LaunchPlan {
 // Kernel launchers (kernels.cu).  All are asynchronous on `st`; `gate` makes a
 // kernel return at once when the run's done flag is set (graph replays).
 cudaError_t setup_kernel_attributes(const LaunchPlan &p);
-int nb_grid_size(int ncols);   // persistent grid of the short-column kernel on the current device
+int bin_grid_size(int ncols);  // persistent grids of the binary and short-column kernels on the current device
+int nb_grid_size(int ncols);
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
 cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st);
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
@@ -207,9 +208,6 @@ constexpr int kHistMaxDomain = 4096;    // largest integer domain of the multi-C
 constexpr int kHistChunk = 16384;       // matrix entries per counting-sort CTA
 constexpr int kHistThreads = 512;
 constexpr int kApplyThreads = 256;
-constexpr int kBinChunk = 2048;         // nonzeros staged in shared memory per binary sub-chunk
-constexpr int kBinTileEntries = 4096;   // target nonzeros of one binary tile
-constexpr int kBinMaxCols = 1024;       // columns of one binary tile
 constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
 
 }  // namespace chap

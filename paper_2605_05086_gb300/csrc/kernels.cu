@@ -65,8 +65,35 @@ __device__ __forceinline__ long long ikey_val(unsigned long long k) { return (lo
 // Sign of a double that is never -0.0 here (margins are eps -+ r rounded to nearest).
 __device__ __forceinline__ bool dneg(double v) { return __double_as_longlong(v) < 0; }
 __device__ __forceinline__ bool dgt(double a, double b) { return dkey(a) > dkey(b); }
-// -v by flipping the sign bit (keeps the FP64 pipe free).
-__device__ __forceinline__ double dflip(double v) { return __longlong_as_double(__double_as_longlong(v) ^ (long long)kSign); }
+// -v by flipping the sign bit in an integer register: written as PTX so that
+// the compiler cannot turn it into an FP64 negation (GB300's FP64 pipe is
+// narrow, and these flips run once per nonzero).
+__device__ __forceinline__ double dflip(double v)
+{
+    long long b;
+    asm("xor.b64 %0, %1, 0x8000000000000000;" : "=l"(b) : "l"(__double_as_longlong(v)));
+    return __longlong_as_double(b);
+}
+
+// Conversions between doubles and integers run on GB300's narrow FP64 pipe;
+// the per-column setup below uses these integer-only forms instead.
+__device__ __forceinline__ bool dfinite(double v) { return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff; }
+
+// Exact int64 value of an integral double with |v| < 2^63.
+__device__ __forceinline__ long long dbl_int(double v)
+{
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0;  // +-0 (an integral double is never subnormal)
+    const long long mant = (b & 0xfffffffffffffLL) | (1LL << 52);
+    const int sh = ex - 1075;  // |v| = mant * 2^sh
+    const long long m = sh >= 0 ? (mant << sh) : (sh <= -53 ? 0 : (mant >> -sh));
+    return b < 0 ? -m : m;
+}
+
+// Float value of an integer with |v| < 2^22: add v to the bits of 1.5 * 2^23
+// and subtract that constant again (both exact; integer and FP32 pipes).
+__device__ __forceinline__ float small_int_f(long long v) { return __int_as_float(0x4B400000 + (int)v) - 12582912.0f; }
 
 // Single-precision estimate of a double from its bits (mantissa truncated,
 // relative error < 2^-23); ok is cleared when |v| is outside the normal float
@@ -133,17 +160,6 @@ __device__ __forceinline__ double i4_double_hi(const int4 &v)
     return __longlong_as_double((long long)(((unsigned long long)(unsigned)v.w << 32) | (unsigned)v.z));
 }
 
-// Position of the column containing nonzero e (s_ptr: nc + 1 column offsets).
-__device__ __forceinline__ int find_col(const int *s_ptr, int nc, int e)
-{
-    int lo = 0, hi = nc - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_ptr[mid] <= e) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Global candidate order: larger score, then lower variable index.
 __device__ __forceinline__ bool cand_better(long long s1, int v1, long long s2, int v2)
 {
@@ -206,18 +222,18 @@ __device__ __forceinline__ ColCtx make_col(const Dev &d, int q, long long iter)
     c.isint = __ldg(d.vtype + j) != kVarCont;
     c.xb = d.x[j];
     const double l = __ldg(d.lb + j), u = __ldg(d.ub + j);
-    const bool fl = isfinite(l), fu = isfinite(u);
+    const bool fl = dfinite(l), fu = dfinite(u);
     c.fok = true;
     if (c.isint) {
-        c.xbi = (long long)c.xb;
+        c.xbi = dbl_int(c.xb);
         c.kxb = ikey(c.xbi);
-        const long long li = fl ? (long long)l : LLONG_MIN, ui = fu ? (long long)u : LLONG_MAX;
+        const long long li = fl ? dbl_int(l) : LLONG_MIN, ui = fu ? dbl_int(u) : LLONG_MAX;
         c.kl = ikey(li);
         c.ku = ikey(ui);
         c.lo = fl ? li - c.xbi : -(1LL << 62);
         c.hi = fu ? ui - c.xbi : (1LL << 62);
-        c.lof = c.lo >= -(1LL << 22) ? (float)c.lo : -INFINITY;
-        c.hif = c.hi <= (1LL << 22) ? (float)c.hi : INFINITY;
+        c.lof = c.lo > -(1LL << 22) ? small_int_f(c.lo) : -INFINITY;
+        c.hif = c.hi < (1LL << 22) ? small_int_f(c.hi) : INFINITY;
         c.dlf = c.duf = c.xaf = 0.0f;
     } else {
         c.xbi = 0;
@@ -336,152 +352,134 @@ __device__ __forceinline__ bool gated_done(const Dev &d, int gate)
 }
 
 // ------------------------------------------------------- binary flip scoring
+//
+// The only move of a binary variable is the flip (Sec. 3.1, "Best Shift
+// Moves"); its score is the sum over the column of the penalty changes of the
+// normalised halves.  A group of kGrp lanes scores one column (four columns
+// per warp, persistent grid over the column quadruples, columns ordered by
+// length): the lanes read the column's nonzeros coalesced, gather the row
+// states and add the penalty changes branch-free in registers; a shuffle
+// reduction closes the column.
 
-// Penalty of moving one normalised half by ad = a * (new - old) (Sec. 3.1,
-// Scoring Functions), integral row with int64 residual r.
-__device__ __forceinline__ void flip_int(long long r, long long ad, long long w, long long &s, int &dc)
+constexpr int kGrp = 8;                      // lanes per column
+constexpr int kGrpPerWarp = 32 / kGrp;       // columns per warp
+constexpr int kEvalWarps = kEvalThreads / 32;
+constexpr int kBinSlots = 1;                 // nonzeros in flight per lane (binary columns)
+constexpr int kNbSlots = 1;                  // nonzeros in flight per lane (short non-binary columns)
+
+// Penalty change of a half in weight units for violated-before v0,
+// violated-after v1 and the sign of the residual change (Sec. 3.1, Scoring
+// Functions): becomes violated -2, becomes satisfied +2, stays violated +1
+// when the residual falls and -1 when it grows (half-weight units).
+__device__ __forceinline__ int flip_f(bool v0, bool v1, bool dec)
 {
-    const long long r1 = r + ad;
-    const bool v0 = r > 0, v1 = r1 > 0;
-    if (!v0 && v1) s -= 2 * w;
-    else if (v0 && !v1) s += 2 * w;
-    else if (v0 && v1) s += (ad < 0) ? w : -w;
-    dc += (int)v1 - (int)v0;
+    return 2 * ((int)v0 - (int)v1) + ((v0 && v1) ? (dec ? 1 : -1) : 0);
 }
 
-// Same on a non-integral row from its margin m = eps - r: violated <=> m < 0,
-// violated after the move <=> ad > m.
-__device__ __forceinline__ void flip_fp(double ad, double m, long long w, long long &s, int &dc)
-{
-    const bool v0 = dneg(m), v1 = dgt(ad, m);
-    if (!v0 && v1) s -= 2 * w;
-    else if (v0 && !v1) s += 2 * w;
-    else if (v0 && v1) s += dneg(ad) ? w : -w;
-    dc += (int)v1 - (int)v0;
-}
-
-// One CSC part of a binary tile: every thread takes aligned groups of 8
-// consecutive nonzeros (two 16-byte loads of row indices, two or four of
-// coefficients), gathers their row states together and scores the flips into
-// per-column accumulators in shared memory.
-template <bool FP>
-__device__ __forceinline__ void bin_part(const Dev &d, int nc, const int *s_ptr, const unsigned char *s_up,
-                                         long long *s_acc, int *s_dc)
-{
-    const int E0 = s_ptr[0], E1 = s_ptr[nc];
-    const int g1 = (E1 + 7) >> 3;
-    for (int g = (E0 >> 3) + threadIdx.x; g < g1; g += blockDim.x) {
-        const int eb = g << 3;
-        int rows[8];
-        {
-            const int4 *rp = reinterpret_cast<const int4 *>((FP ? d.cf_row : d.ci_row) + eb);
-            const int4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-            rows[0] = r0.x; rows[1] = r0.y; rows[2] = r0.z; rows[3] = r0.w;
-            rows[4] = r1.x; rows[5] = r1.y; rows[6] = r1.z; rows[7] = r1.w;
-        }
-        double dv[8];
-        int iv[8];
-        if (FP) {
-            const double2 *vp = reinterpret_cast<const double2 *>(d.cf_val + eb);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { const double2 v = __ldg(vp + k); dv[2 * k] = v.x; dv[2 * k + 1] = v.y; }
-        } else {
-            const int4 *vp = reinterpret_cast<const int4 *>(d.ci_val + eb);
-            const int4 v0 = __ldg(vp), v1 = __ldg(vp + 1);
-            iv[0] = v0.x; iv[1] = v0.y; iv[2] = v0.z; iv[3] = v0.w;
-            iv[4] = v1.x; iv[5] = v1.y; iv[6] = v1.z; iv[7] = v1.w;
-        }
-        int col = find_col(s_ptr, nc, max(eb, E0));
-        long long acc = 0;
-        int accd = 0;
-        constexpr int B = FP ? 4 : 8;
-#pragma unroll
-        for (int b0 = 0; b0 < 8; b0 += B) {
-            int4 st0[B], st1[B];
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int e = eb + b0 + q;
-                if (e >= E0 && e < E1) {
-                    const int4 *pp = reinterpret_cast<const int4 *>(d.rs + rows[b0 + q]);
-                    st0[q] = __ldg(pp);
-                    if (FP) st1[q] = __ldg(pp + 1);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int e = eb + b0 + q;
-                if (e < E0 || e >= E1) continue;
-                while (s_ptr[col + 1] <= e) {
-                    if (acc | accd) {
-                        atomicAdd(reinterpret_cast<unsigned long long *>(s_acc + col), (unsigned long long)acc);
-                        atomicAdd(s_dc + col, accd);
-                    }
-                    acc = 0;
-                    accd = 0;
-                    ++col;
-                }
-                const bool up = s_up[col] != 0;
-                if (FP) {
-                    const double ad = up ? dv[b0 + q] : dflip(dv[b0 + q]);
-                    flip_fp(ad, i4_double_lo(st1[q]), st0[q].z, acc, accd);
-                    if (st0[q].w >= 0) flip_fp(dflip(ad), i4_double_hi(st1[q]), st0[q].w, acc, accd);
-                } else {
-                    const long long ad = up ? (long long)iv[b0 + q] : -(long long)iv[b0 + q];
-                    const long long r = row_r(st0[q]);
-                    flip_int(r, ad, st0[q].z, acc, accd);
-                    if (st0[q].w >= 0) flip_int(-r, -ad, st0[q].w, acc, accd);
-                }
-            }
-        }
-        if (acc | accd) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(s_acc + col), (unsigned long long)acc);
-            atomicAdd(s_dc + col, accd);
-        }
-    }
-}
-
-// Binary columns at positions [tile.begin, tile.end): their nonzeros are
-// contiguous in both CSC matrices, so the tile streams two flat ranges.
-__global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, const Tile *tiles, VarOut o, int gate)
+__global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, VarOut o, int gate)
 {
     if (gated_done(d, gate)) return;
-    __shared__ int s_pi[kBinMaxCols + 1];
-    __shared__ int s_pf[kBinMaxCols + 1];
-    __shared__ long long s_acc[kBinMaxCols];
-    __shared__ int s_dc[kBinMaxCols];
-    __shared__ unsigned char s_up[kBinMaxCols];
-    const Tile tl = tiles[blockIdx.x];
-    const int q0 = tl.begin, nc = tl.end - tl.begin;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        s_acc[c] = 0;
-        s_dc[c] = 0;
-        s_up[c] = __double_as_longlong(d.x[__ldg(d.var_list + q0 + c)]) == 0;  // flip 0 -> 1
-    }
-    for (int c = threadIdx.x; c <= nc; c += blockDim.x) {
-        s_pi[c] = __ldg(d.ci_ptr + q0 + c);
-        s_pf[c] = __ldg(d.cf_ptr + q0 + c);
-    }
-    __syncthreads();
-    bin_part<false>(d, nc, s_pi, s_up, s_acc, s_dc);
-    bin_part<true>(d, nc, s_pf, s_up, s_acc, s_dc);
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / kGrp, sub = lane & (kGrp - 1);
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
     Cand best{0, kNoVar, 0, 0.0};
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int j = __ldg(d.var_list + q0 + c);
-        const bool up = s_up[c] != 0;
-        const long long sc = s_acc[c];
-        const int dc = s_dc[c];
-        bool mv = sc > 0;
-        if (mv) {
-            const int stamp = up ? d.tabu_inc[j] : d.tabu_dec[j];
-            mv = iter >= (long long)stamp || nviol + (long long)dc < bestnv;
+    const int nquad = (ncols + kGrpPerWarp - 1) / kGrpPerWarp;
+    for (int qd = blockIdx.x * kEvalWarps + warp; qd < nquad; qd += gridDim.x * kEvalWarps) {
+        const int q = qd * kGrpPerWarp + g;
+        const bool live = q < ncols;
+        const int qq = live ? q : 0;
+        const int ci0 = __ldg(d.ci_ptr + qq), cf0 = __ldg(d.cf_ptr + qq);
+        const int nI = live ? __ldg(d.ci_ptr + qq + 1) - ci0 : 0;
+        const int nF = live ? __ldg(d.cf_ptr + qq + 1) - cf0 : 0;
+        const int j = __ldg(d.var_list + qq);
+        const bool up = __double_as_longlong(d.x[j]) == 0;  // flip 0 -> 1
+        long long s = 0;
+        int dc = 0;
+        int nImax = nI, nFmax = nF;
+#pragma unroll
+        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) {
+            nImax = max(nImax, __shfl_xor_sync(FULLMASK, nImax, o2));
+            nFmax = max(nFmax, __shfl_xor_sync(FULLMASK, nFmax, o2));
         }
-        const double xh = up ? 1.0 : 0.0;
-        if (o.xhat) o.xhat[j] = mv ? xh : d.x[j];
-        if (o.s) o.s[j] = mv ? sc : 0;
-        if (o.dc) o.dc[j] = mv ? dc : 0;
-        if (mv && cand_better(sc, j, best.s, best.var)) best = Cand{sc, j, dc, xh};
+        // integral rows: r1 = r + a (x_j rises) or r - a; the second half of an
+        // "=" row has residual -r and change -(r1 - r)
+        for (int base = 0; base < nImax; base += kBinSlots * kGrp) {
+            int row[kBinSlots], av[kBinSlots];
+#pragma unroll
+            for (int k = 0; k < kBinSlots; ++k) {
+                const int v = base + k * kGrp + sub;
+                const bool ok = v < nI;
+                row[k] = ok ? __ldg(d.ci_row + ci0 + v) : 0;
+                av[k] = ok ? __ldg(d.ci_val + ci0 + v) : 0;
+            }
+            int4 st[kBinSlots];
+#pragma unroll
+            for (int k = 0; k < kBinSlots; ++k) st[k] = av[k] != 0 ? ld_row16(d.rs + row[k]) : make_int4(0, 0, 0, -1);
+#pragma unroll
+            for (int k = 0; k < kBinSlots; ++k) {
+                const long long r = row_r(st[k]);
+                const int ad = up ? av[k] : -av[k];
+                const long long r1 = r + ad;
+                const bool v0 = r > 0, v1 = r1 > 0;
+                s += (long long)flip_f(v0, v1, ad < 0) * st[k].z;
+                dc += (int)v1 - (int)v0;
+                const bool two = st[k].w >= 0;
+                const bool u0 = two && r < 0, u1 = two && r1 < 0;
+                s += (long long)flip_f(u0, u1, ad > 0) * (two ? st[k].w : 0);
+                dc += (int)u1 - (int)u0;
+            }
+        }
+        // non-integral rows: violated <=> m < 0 with m = eps - r of the half;
+        // violated after the move <=> (change of r) > m
+        for (int base = 0; base < nFmax; base += kBinSlots * kGrp) {
+            int row[kBinSlots];
+            double av[kBinSlots];
+            bool ok[kBinSlots];
+#pragma unroll
+            for (int k = 0; k < kBinSlots; ++k) {
+                const int v = base + k * kGrp + sub;
+                ok[k] = v < nF;
+                row[k] = ok[k] ? __ldg(d.cf_row + cf0 + v) : 0;
+                av[k] = ok[k] ? __ldg(d.cf_val + cf0 + v) : 0.0;
+            }
+            int4 s0[kBinSlots], s1[kBinSlots];
+#pragma unroll
+            for (int k = 0; k < kBinSlots; ++k) {
+                const int4 *p = reinterpret_cast<const int4 *>(d.rs + row[k]);
+                s0[k] = ok[k] ? __ldg(p) : make_int4(0, 0, 0, -1);
+                s1[k] = ok[k] ? __ldg(p + 1) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < kBinSlots; ++k) {
+                const double ad = up ? av[k] : dflip(av[k]);
+                const double m1 = i4_double_lo(s1[k]), m2 = i4_double_hi(s1[k]);
+                const bool neg = dneg(ad);
+                const bool v0 = dneg(m1), v1 = dgt(ad, m1);
+                s += (long long)flip_f(v0, v1, neg) * s0[k].z;
+                dc += (int)v1 - (int)v0;
+                const bool two = s0[k].w >= 0;
+                const bool u0 = two && dneg(m2), u1 = two && dgt(dflip(ad), m2);
+                s += (long long)flip_f(u0, u1, !neg) * (two ? s0[k].w : 0);
+                dc += (int)u1 - (int)u0;
+            }
+        }
+#pragma unroll
+        for (int o2 = kGrp >> 1; o2 > 0; o2 >>= 1) {
+            s += __shfl_xor_sync(FULLMASK, s, o2);
+            dc += __shfl_xor_sync(FULLMASK, dc, o2);
+        }
+        if (sub == 0 && live) {
+            bool mv = s > 0;
+            if (mv) {
+                const int stamp = up ? d.tabu_inc[j] : d.tabu_dec[j];
+                mv = iter >= (long long)stamp || nviol + (long long)dc < bestnv;
+            }
+            const double xh = up ? 1.0 : 0.0;
+            if (o.xhat) o.xhat[j] = mv ? xh : d.x[j];
+            if (o.s) o.s[j] = mv ? s : 0;
+            if (o.dc) o.dc[j] = mv ? dc : 0;
+            if (mv && cand_better(s, j, best.s, best.var)) best = Cand{s, j, dc, xh};
+        }
     }
     const Cand b = block_reduce_cand(best);
     if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
@@ -727,9 +725,7 @@ __device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, u
 //     admissible candidate.  A column whose list outgrows kGrpStage entries is
 //     evaluated again by the whole warp with a list of kWarpSortMax entries.
 
-constexpr int kNbWarps = kEvalThreads / 32;
-constexpr int kGrp = 8;                      // lanes per column
-constexpr int kGrpPerWarp = 32 / kGrp;       // columns per warp
+constexpr int kNbWarps = kEvalWarps;
 constexpr int kGrpStage = 4 * kGrp;          // list entries per column on the group path
 constexpr int kQCap = 32 + 4 * 32 - 1;      // queued halves per warp: < 32 left + one round of 4 halves per lane
 static_assert(kGrpPerWarp * kGrpStage == kWarpSortMax, "the whole-warp path reuses the group lists");
@@ -775,21 +771,35 @@ struct __align__(16) NbWarp {
 };
 constexpr int kNbSmem = kNbWarps * (int)sizeof(NbWarp);   // dynamic shared memory of k_eval_nb
 
-// Single-precision estimate of an int64 (relative error < 2^-23).
-__device__ __forceinline__ float ll_approx(long long v)
+// Scalars of a decided half as multiples of its weight, branch-free: the case
+// table of Algorithm 1 (as in half_case / half_acc) for index
+// T*8 + P*4 + V*2 + L (T tight, P a > 0, V violated, L left of l; a half right
+// of u has L = 0), packed as mb + 2 (3 bits), ma / 2 + 1, bc + 1, ac + 1
+// (2 bits each), where beta += mb w, alpha += ma w, beta_c += bc,
+// alpha_c += ac.  Index 1 adds nothing (used for inactive or queued halves).
+constexpr unsigned long long kTabB = 0x492000702450ull;
+constexpr unsigned kTabA = 0xaa05a5u, kTabBC = 0x55aa4916u, kTabAC = 0xaa005555u;
+
+__device__ __forceinline__ void acc_decided(int idx, int w, Acc &acc)
 {
-    return (v >= INT_MIN && v <= INT_MAX) ? (float)(int)v : __ll2float_rn(v);
+    const int mb = (int)((kTabB >> (3 * idx)) & 7ull) - 2;
+    const int ma = 2 * ((int)((kTabA >> (2 * idx)) & 3u) - 1);
+    acc.beta += (long long)mb * w;
+    acc.alpha += (long long)ma * w;
+    acc.beta_c += (int)((kTabBC >> (2 * idx)) & 3u) - 1;
+    acc.alpha_c += (int)((kTabAC >> (2 * idx)) & 3u) - 1;
 }
 
-// Place the breakpoint of a half by products: z / a against the thresholds
-// L (left of l) and U (right of u) of the column, a > 0 after normalisation.
-// Returns -1 / +1 when certain, else 0.
-__device__ __forceinline__ int side_of(float z, float a, float L, float U, float tol)
+// Side of a breakpoint from single-precision products (z / a against the
+// thresholds L, U of the column, a > 0 after normalisation), with relative
+// margins covering the float estimates and an absolute term tol: sets left /
+// right only when certain.
+__device__ __forceinline__ void side_test(float z, float a, float L, float U, float tol, bool &left, bool &right)
 {
     const float P = L * a, Q = U * a;
-    if (z + slack(z) + tol < P - slack(P)) return -1;
-    if (z - slack(z) - tol > Q + slack(Q)) return 1;
-    return 0;
+    const float az = fabsf(z) * 1.0e-5f + tol + 1.0e-30f;
+    left = z + az < P - (fabsf(P) * 1.0e-5f + 1.0e-30f);
+    right = z - az > Q + (fabsf(Q) * 1.0e-5f + 1.0e-30f);
 }
 
 // Exact breakpoint of one queued half (Algorithm 1 case table, as int_half /
@@ -824,7 +834,7 @@ __device__ __forceinline__ void exact_item(const QItem &it, const ColCtx &ci, Ac
 }
 
 // Exact pass over n <= 32 queued halves starting at ring position head, one per lane.
-__device__ __forceinline__ void flush_queue(NbWarp &W, int head, int n, int lane)
+__device__ __noinline__ void flush_queue(NbWarp &W, int head, int n, int lane)
 {
     if (lane < n) {
         int pos = head + lane;
@@ -982,7 +992,7 @@ __device__ __noinline__ void column_warp(const Dev &d, const VarOut &o, int q, S
     const int nv = c.nI + c.nF;
     int cnt;
     {
-        const bool fl = isfinite(__ldg(d.lb + c.j)), fu = isfinite(__ldg(d.ub + c.j));
+        const bool fl = dfinite(__ldg(d.lb + c.j)), fu = dfinite(__ldg(d.ub + c.j));
         if (lane == 0) {
             if (fl) stage[0] = SEnt{c.kl, 0, make_aux(0, 0)};
             if (fu) stage[fl ? 1 : 0] = SEnt{c.ku, 0, make_aux(0, 0)};
@@ -1032,6 +1042,7 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
         const bool live = cq < ncols;
         int nI, nv, ci0, cf0;
         float Lp, Ln, Up, Un, tolf;
+        long long ilo, ihi;
         bool fok, isint;
         {
             const ColCtx c = make_col(d, q0 + (live ? cq : 0), iter);
@@ -1046,6 +1057,8 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
             // z/a <= lo - 1 (a < 0); t > u <=> z/a >= hi + 1 (a > 0) or z/a > hi
             // (a < 0).  Continuous (z = -r): t < l <=> z/a < l - xbar,
             // t > u <=> z/a > u - xbar, with a margin for the rounding of t.
+            ilo = c.lo;
+            ihi = c.hi;
             Lp = isint ? c.lof : -c.dlf;
             Ln = isint ? c.lof - 1.0f : -c.dlf;
             Up = isint ? c.hif + 1.0f : -c.duf;
@@ -1056,8 +1069,8 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
                 W.beta[g] = 0; W.alpha[g] = 0; W.beta_c[g] = 0; W.alpha_c[g] = 0;
                 int n = 0;
                 if (live) {
-                    if (isfinite(__ldg(d.lb + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.kl, 0, make_aux(0, 0)};
-                    if (isfinite(__ldg(d.ub + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.ku, 0, make_aux(0, 0)};
+                    if (dfinite(__ldg(d.lb + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.kl, 0, make_aux(0, 0)};
+                    if (dfinite(__ldg(d.ub + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.ku, 0, make_aux(0, 0)};
                 }
                 W.cnt[g] = n;
             }
@@ -1065,89 +1078,113 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
         __syncwarp();
         int head = 0, qn = 0;
         Acc acc{0, 0, 0, 0};
-        int nvmax = nv;
+        int nImax = nI, nFmax = nv - nI;
 #pragma unroll
-        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) nvmax = max(nvmax, __shfl_xor_sync(FULLMASK, nvmax, o2));
-        for (int base = 0; base < nvmax; base += 2 * kGrp) {
-            int row[2];
-            long long ai[2];
-            double ad[2];
-            bool ok[2], fp[2];
+        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) {
+            nImax = max(nImax, __shfl_xor_sync(FULLMASK, nImax, o2));
+            nFmax = max(nFmax, __shfl_xor_sync(FULLMASK, nFmax, o2));
+        }
+        // integral rows (integer variables only): exact int64 r and a
+        for (int base = 0; base < nImax; base += kNbSlots * kGrp) {
+            int row[kNbSlots], av[kNbSlots];
+            bool ok[kNbSlots];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < kNbSlots; ++k) {
                 const int v = base + k * kGrp + sub;
-                ok[k] = v < nv;
-                fp[k] = v >= nI;
-                row[k] = 0;
-                ai[k] = 0;
-                ad[k] = 0.0;
-                if (ok[k]) {
-                    if (fp[k]) {
-                        const int e = cf0 + (v - nI);
-                        row[k] = __ldg(d.cf_row + e);
-                        ad[k] = __ldg(d.cf_val + e);
-                    } else {
-                        const int e = ci0 + v;
-                        row[k] = __ldg(d.ci_row + e);
-                        ai[k] = __ldg(d.ci_val + e);
-                    }
-                }
+                ok[k] = v < nI;
+                row[k] = ok[k] ? __ldg(d.ci_row + ci0 + v) : 0;
+                av[k] = ok[k] ? __ldg(d.ci_val + ci0 + v) : 1;
             }
-            int4 s0[2], s1[2];
+            int4 s0[kNbSlots];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                s0[k] = make_int4(0, 0, 0, -1);
-                s1[k] = make_int4(0, 0, 0, 0);
-                if (ok[k]) {
-                    const int4 *p = reinterpret_cast<const int4 *>(d.rs + row[k]);
-                    s0[k] = __ldg(p);
-                    if (fp[k]) s1[k] = __ldg(p + 1);
-                }
-            }
+            for (int k = 0; k < kNbSlots; ++k) s0[k] = ok[k] ? ld_row16(d.rs + row[k]) : make_int4(0, 0, 0, -1);
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < kNbSlots; ++k) {
+                const long long r1 = row_r(s0[k]);
 #pragma unroll
                 for (int hf = 0; hf < 2; ++hf) {
-                    const int w = hf ? s0[k].w : s0[k].z;
                     const bool act = ok[k] && (hf == 0 || s0[k].w >= 0);
-                    bool viol, apos, tight0 = false, fin = true;
-                    float zf, af;
-                    long long qx, qa;
-                    if (!fp[k]) {
-                        const long long r = hf ? -row_r(s0[k]) : row_r(s0[k]);
-                        const long long a = hf ? -ai[k] : ai[k];
-                        viol = r > 0;
-                        apos = a > 0;
-                        zf = ll_approx(-r);
-                        af = (float)a;
-                        qx = r;
-                        qa = a;
-                    } else {
-                        const double r0 = i4_double_lo(s0[k]);
-                        const double r = hf ? dflip(r0) : r0, a = hf ? dflip(ad[k]) : ad[k];
-                        const double m = hf ? i4_double_hi(s1[k]) : i4_double_lo(s1[k]);
-                        const double mo = hf ? i4_double_lo(s1[k]) : i4_double_hi(s1[k]);
-                        viol = dneg(m);
-                        apos = !dneg(a);
-                        tight0 = !isint && !viol && !dneg(mo);  // |r| <= eps: tight wherever t is
-                        fin = fok;
-                        zf = approx_f(isint ? m : dflip(r), fin);
-                        af = approx_f(a, fin);
-                        qx = __double_as_longlong(isint ? m : r);
-                        qa = __double_as_longlong(a);
-                    }
-                    int side = 0;
-                    if (fin) {
-                        if (!apos) { zf = -zf; af = -af; }
-                        side = side_of(zf, af, apos ? Lp : Ln, apos ? Up : Un, tolf * af);
-                    }
-                    if (act && (tight0 || side != 0)) half_acc(viol, tight0, apos, side, w, acc);
-                    const bool pend = act && !tight0 && side == 0;
+                    if (hf == 1 && !__any_sync(FULLMASK, act)) continue;
+                    const long long r = hf ? -r1 : r1;
+                    const int a = hf ? -av[k] : av[k];
+                    const int w = hf ? s0[k].w : s0[k].z;
+                    const bool V = r > 0, P = a > 0;
+                    // exact side test with z = -r, aa = a (a > 0) or z = r, aa = -a:
+                    // t < l <=> z <= L' aa - [a > 0], t > u <=> z > H' aa - [a > 0] with
+                    // L' = lo, H' = hi + 1 (a > 0) or L' = lo - 1, H' = hi (a < 0);
+                    // |lo a|, |hi a| <= 2^53 on integral rows
+                    const long long z = P ? -r : r;
+                    const long long aa = P ? a : -a;
+                    const long long Lz = (P ? ilo : ilo - 1) * aa - (long long)P;
+                    const long long Rz = (P ? ihi + 1 : ihi) * aa - (long long)P;
+                    const bool left = z <= Lz, right = z > Rz;
+                    const bool dec = act && (left || right);
+                    acc_decided(dec ? (((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
+                    const bool pend = act && !dec;
                     const unsigned bal = __ballot_sync(FULLMASK, pend);
                     if (pend) {
                         int pos = head + qn + __popc(bal & ((1u << lane) - 1u));
                         if (pos >= kQCap) pos -= kQCap;
-                        W.q[pos] = QItem{qx, qa, w, g | ((int)fp[k] << 2) | ((int)viol << 3)};
+                        W.q[pos] = QItem{r, (long long)a, w, g | ((int)V << 3)};
+                    }
+                    qn += __popc(bal);
+                }
+            }
+            __syncwarp();
+            while (qn >= 32) {
+                flush_queue(W, head, 32, lane);
+                head += 32;
+                if (head >= kQCap) head -= kQCap;
+                qn -= 32;
+            }
+        }
+        // non-integral rows: margins m = eps - r, mo = eps + r of the half
+        for (int base = 0; base < nFmax; base += kNbSlots * kGrp) {
+            int row[kNbSlots];
+            double av[kNbSlots];
+            bool ok[kNbSlots];
+#pragma unroll
+            for (int k = 0; k < kNbSlots; ++k) {
+                const int v = nI + base + k * kGrp + sub;
+                ok[k] = v < nv;
+                row[k] = ok[k] ? __ldg(d.cf_row + cf0 + (v - nI)) : 0;
+                av[k] = ok[k] ? __ldg(d.cf_val + cf0 + (v - nI)) : 1.0;
+            }
+            int4 s0[kNbSlots], s1[kNbSlots];
+#pragma unroll
+            for (int k = 0; k < kNbSlots; ++k) {
+                const int4 *p = reinterpret_cast<const int4 *>(d.rs + row[k]);
+                s0[k] = ok[k] ? __ldg(p) : make_int4(0, 0, 0, -1);
+                s1[k] = ok[k] ? __ldg(p + 1) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < kNbSlots; ++k) {
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    const bool act = ok[k] && (hf == 0 || s0[k].w >= 0);
+                    if (hf == 1 && !__any_sync(FULLMASK, act)) continue;
+                    const double r0 = i4_double_lo(s0[k]);
+                    const double r = hf ? dflip(r0) : r0, a = hf ? dflip(av[k]) : av[k];
+                    const double m = hf ? i4_double_hi(s1[k]) : i4_double_lo(s1[k]);
+                    const double mo = hf ? i4_double_lo(s1[k]) : i4_double_hi(s1[k]);
+                    const int w = hf ? s0[k].w : s0[k].z;
+                    const bool V = dneg(m), P = !dneg(a);
+                    const bool T = !isint && !V && !dneg(mo);  // |r| <= eps: tight wherever t is
+                    // z = m (integer variable) or -r (continuous); a > 0 after flipping both
+                    const double z0 = isint ? m : dflip(r);
+                    bool fin = fok;
+                    const float zf = approx_f(P ? z0 : dflip(z0), fin), af = approx_f(P ? a : dflip(a), fin);
+                    bool left = false, right = false;
+                    if (fin) side_test(zf, af, P ? Lp : Ln, P ? Up : Un, tolf * af, left, right);
+                    const bool dec = act && (T || left || right);
+                    acc_decided(dec ? (((int)T << 3) | ((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
+                    const bool pend = act && !dec;
+                    const unsigned bal = __ballot_sync(FULLMASK, pend);
+                    if (pend) {
+                        int pos = head + qn + __popc(bal & ((1u << lane) - 1u));
+                        if (pos >= kQCap) pos -= kQCap;
+                        W.q[pos] = QItem{__double_as_longlong(isint ? m : r), __double_as_longlong(a), w,
+                                         g | 4 | ((int)V << 3)};
                     }
                     qn += __popc(bal);
                 }
@@ -1253,7 +1290,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
     const ColCtx c = make_col(d, tl.begin, iter);
     const double l = __ldg(d.lb + c.j), u = __ldg(d.ub + c.j);
-    const bool fl = isfinite(l), fu = isfinite(u);
+    const bool fl = dfinite(l), fu = dfinite(u);
     if (threadIdx.x == 0) {
         s_cnt = (fl ? 1 : 0) + (fu ? 1 : 0);
         s_beta = 0; s_alpha = 0; s_bc = 0; s_ac = 0;
@@ -1694,6 +1731,23 @@ static int grid_for(long long n, int threads, int cap = 152 * 8)
     return (int)g;
 }
 
+int bin_grid_size(int ncols)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_bin, kEvalThreads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    const long long need = ((long long)ncols + kEvalWarps * kGrpPerWarp - 1) / (kEvalWarps * kGrpPerWarp);
+    const long long cap = (long long)sms * per_sm;
+    return (int)(need < cap ? need : cap);
+}
+
 int nb_grid_size(int ncols)
 {
     // one resident wave: every SM holds as many CTAs as fit, and no CTA is
@@ -1709,7 +1763,7 @@ int nb_grid_size(int ncols)
         cudaGetLastError();
         sms = 152;
     }
-    const long long need = ((long long)ncols + kNbWarps - 1) / kNbWarps;
+    const long long need = ((long long)ncols + kNbWarps * kGrpPerWarp - 1) / (kNbWarps * kGrpPerWarp);
     const long long cap = (long long)sms * per_sm;
     return (int)(need < cap ? need : cap);
 }
@@ -1736,7 +1790,7 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (side[k]) e = cudaStreamWaitEvent(p.side[k], p.ev_fork, 0);
     if (e != cudaSuccess) return e;
-    if (p.n_bin) k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.tiles_bin, o, gate);
+    if (p.n_bin) k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate);
     if (p.nb_grid) k_eval_nb<<<p.nb_grid, kEvalThreads, kNbSmem, p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
     if (p.n_cta) k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
     if (p.n_hist_tiles) k_eval_hist<<<p.n_hist_tiles, kHistThreads, p.hist_smem, p.side[2]>>>(d, p.tiles_hist, o, gate);
