@@ -397,7 +397,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     for (int q = 0; q < n; ++q) vpos[var_list[q]] = q;
 
     // ---- split CSC in var_list order (integral rows: int32 coefficients; others: double)
-    std::vector<int> ci_ptr(n + 1, 0), cf_ptr(n + 1, 0);
+    //      inside each part the rows of one normalised half come first and the
+    //      "=" rows (two halves) after them, from ci_eq[q] / cf_eq[q] on
+    std::vector<int> ci_ptr(n + 1, 0), cf_ptr(n + 1, 0), ci_eq(n, 0), cf_eq(n, 0);
     std::vector<int> ci_row, ci_val, cf_row;
     std::vector<double> cf_val;
     ci_row.reserve(nnz_int);
@@ -406,11 +408,18 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     cf_val.reserve(p->nnz - nnz_int);
     for (int q = 0; q < n; ++q) {
         const int j = var_list[q];
-        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) {
-            const int i = p->row_idx[e];
-            const double a = sign[i] * p->col_val[e];
-            if (rint[i]) { ci_row.push_back(i); ci_val.push_back((int)a); }
-            else { cf_row.push_back(i); cf_val.push_back(a); }
+        for (int eq = 0; eq < 2; ++eq) {
+            if (eq) {
+                ci_eq[q] = (int)ci_row.size();
+                cf_eq[q] = (int)cf_row.size();
+            }
+            for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) {
+                const int i = p->row_idx[e];
+                if ((h->row_eq[i] != 0) != (eq != 0)) continue;
+                const double a = sign[i] * p->col_val[e];
+                if (rint[i]) { ci_row.push_back(i); ci_val.push_back((int)a); }
+                else { cf_row.push_back(i); cf_val.push_back(a); }
+            }
         }
         ci_ptr[q + 1] = (int)ci_row.size();
         cf_ptr[q + 1] = (int)cf_row.size();
@@ -467,6 +476,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     cf_row.resize(cf_row.size() + 8, 0); cf_val.resize(cf_val.size() + 8, 0.0);
     int *ci_ptr_d = dalloc<int>(h, n + 1), *ci_row_d = dalloc<int>(h, ci_row.size()), *ci_val_d = dalloc<int>(h, ci_val.size());
     int *cf_ptr_d = dalloc<int>(h, n + 1), *cf_row_d = dalloc<int>(h, cf_row.size());
+    int *ci_eq_d = dalloc<int>(h, n), *cf_eq_d = dalloc<int>(h, n);
     double *cf_val_d = dalloc<double>(h, cf_val.size());
     long long *row_ptr_d = dalloc<long long>(h, m + 1);
     int *col_idx_d = dalloc<int>(h, p->nnz);
@@ -495,7 +505,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     h->t_w = dalloc<int>(h, mn);
     h->t_r = dalloc<double>(h, mn);
     h->t_tabu = dalloc<long long>(h, n);
-    bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && row_ptr_d && col_idx_d &&
+    bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && ci_eq_d && cf_eq_d && row_ptr_d && col_idx_d &&
               row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.rs &&
               d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
               d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
@@ -512,6 +522,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
     d.ci_ptr = ci_ptr_d; d.ci_row = ci_row_d; d.ci_val = ci_val_d;
     d.cf_ptr = cf_ptr_d; d.cf_row = cf_row_d; d.cf_val = cf_val_d;
+    d.ci_eq = ci_eq_d; d.cf_eq = cf_eq_d;
     d.row_ptr = row_ptr_d; d.col_idx = col_idx_d; d.row_val = row_val_d;
     d.rhs = rhs_d; d.eps = eps_d; d.row_int = rint_d; d.nrow_base = nrb_d;
     d.vtype = vt_d; d.lb = lb_d; d.ub = ub_d; d.obj = obj_d;
@@ -524,6 +535,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
 #define UP(dst, src, cnt) if (e == cudaSuccess) e = h2d(dst, src, cnt, st)
     UP(ci_ptr_d, ci_ptr.data(), n + 1); UP(ci_row_d, ci_row.data(), ci_row.size()); UP(ci_val_d, ci_val.data(), ci_val.size());
     UP(cf_ptr_d, cf_ptr.data(), n + 1); UP(cf_row_d, cf_row.data(), cf_row.size()); UP(cf_val_d, cf_val.data(), cf_val.size());
+    UP(ci_eq_d, ci_eq.data(), n); UP(cf_eq_d, cf_eq.data(), n);
     UP(row_ptr_d, rp.data(), m + 1); UP(col_idx_d, p->col_idx, p->nnz); UP(row_val_d, row_val.data(), p->nnz);
     UP(rhs_d, rhs.data(), m); UP(eps_d, eps.data(), m); UP(rint_d, rint.data(), m); UP(nrb_d, h->nrow_base.data(), m);
     UP(vt_d, p->vtype, n); UP(lb_d, p->lb, n); UP(ub_d, p->ub, n); UP(obj_d, h->obj.data(), n);

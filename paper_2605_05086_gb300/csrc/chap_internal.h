@@ -18,7 +18,10 @@
 //    double coefficient: 12 B/nnz).  Columns are stored in evaluation order
 //    var_list (binary columns first, then each non-binary class), so the
 //    binary pass streams one contiguous range; position q (var_list[q] = j,
-//    vpos[j] = q) owns ci_ptr[q]..ci_ptr[q+1] and cf_ptr[q]..cf_ptr[q+1].  The
+//    vpos[j] = q) owns ci_ptr[q]..ci_ptr[q+1] and cf_ptr[q]..cf_ptr[q+1], the
+//    rows of one normalised half first and the "=" rows (two halves) from
+//    ci_eq[q] / cf_eq[q] on, so that the kernels run the second-half code only
+//    where it has work.  The
 //    arithmetic type of a nonzero is known from the matrix it sits in, so no
 //    per-row flag is gathered.
 //  - CSR (double) of the physical rows, used only to recompute residuals from
@@ -125,6 +128,9 @@ struct Dev {
     const int *ci_ptr, *ci_row, *ci_val;
     const int *cf_ptr, *cf_row;
     const double *cf_val;
+    // inside each column part the single rows come first, the "=" rows from
+    // ci_eq[q] / cf_eq[q] on
+    const int *ci_eq, *cf_eq;
     // CSR of the physical rows (set-state only)
     const long long *row_ptr;
     const int *col_idx;

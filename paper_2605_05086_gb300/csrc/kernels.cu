@@ -364,8 +364,6 @@ __device__ __forceinline__ bool gated_done(const Dev &d, int gate)
 constexpr int kGrp = 8;                      // lanes per column
 constexpr int kGrpPerWarp = 32 / kGrp;       // columns per warp
 constexpr int kEvalWarps = kEvalThreads / 32;
-constexpr int kBinSlots = 1;                 // nonzeros in flight per lane (binary columns)
-constexpr int kNbSlots = 1;                  // nonzeros in flight per lane (short non-binary columns)
 
 // Penalty change of a half in weight units for violated-before v0,
 // violated-after v1 and the sign of the residual change (Sec. 3.1, Scoring
@@ -374,6 +372,75 @@ constexpr int kNbSlots = 1;                  // nonzeros in flight per lane (sho
 __device__ __forceinline__ int flip_f(bool v0, bool v1, bool dec)
 {
     return 2 * ((int)v0 - (int)v1) + ((v0 && v1) ? (dec ? 1 : -1) : 0);
+}
+
+// Largest value of v over the four groups of the warp.
+__device__ __forceinline__ int quad_max(int v)
+{
+#pragma unroll
+    for (int o2 = 16; o2 >= kGrp; o2 >>= 1) v = max(v, __shfl_xor_sync(FULLMASK, v, o2));
+    return v;
+}
+
+// Flip score terms of one nonzero of an integral row (int64 residual r; a rise
+// of x_j changes r by a; the second half of an "=" row has residual -r and
+// change -a) and of a non-integral row (below).
+template <bool EQ>
+__device__ __forceinline__ void flip_int(const int4 &st, int av, bool up, long long &s, int &dc)
+{
+    const long long r = row_r(st);
+    const int ad = up ? av : -av;
+    const long long r1 = r + ad;
+    const bool v0 = r > 0, v1 = r1 > 0;
+    s += (long long)flip_f(v0, v1, ad < 0) * st.z;
+    dc += (int)v1 - (int)v0;
+    if (EQ) {
+        const bool u0 = r < 0, u1 = r1 < 0;
+        s += (long long)flip_f(u0, u1, ad > 0) * st.w;
+        dc += (int)u1 - (int)u0;
+    }
+}
+
+// Non-integral row: violated <=> m < 0 with m = eps - r of the half; violated
+// after the move <=> change > m.
+template <bool EQ>
+__device__ __forceinline__ void flip_fp(const int4 &s0, const int4 &s1, double av, bool up, long long &s, int &dc)
+{
+    const double ad = up ? av : dflip(av);
+    const bool neg = dneg(ad);
+    const double m1 = i4_double_lo(s1);
+    const bool v0 = dneg(m1), v1 = dgt(ad, m1);
+    s += (long long)flip_f(v0, v1, neg) * s0.z;
+    dc += (int)v1 - (int)v0;
+    if (EQ) {
+        const double m2 = i4_double_hi(s1);
+        const bool u0 = dneg(m2), u1 = dgt(dflip(ad), m2);
+        s += (long long)flip_f(u0, u1, !neg) * s0.w;
+        dc += (int)u1 - (int)u0;
+    }
+}
+
+// Flip scores of one part of a column (FP: non-integral rows; EQ: "=" rows,
+// both halves), one nonzero per lane and round.
+template <bool FP, bool EQ>
+__device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, int sub, bool up, long long &s, int &dc)
+{
+    for (int base = 0; base < nmax; base += kGrp) {
+        const int v = base + sub;
+        const bool ok = v < n;
+        const int row = ok ? __ldg((FP ? d.cf_row : d.ci_row) + e0 + v) : 0;
+        const int4 z4 = make_int4(0, 0, 0, 0);
+        if (!FP) {
+            const int av = ok ? __ldg(d.ci_val + e0 + v) : 0;
+            const int4 st = ok ? ld_row16(d.rs + row) : z4;
+            flip_int<EQ>(st, av, up, s, dc);
+        } else {
+            const double av = ok ? __ldg(d.cf_val + e0 + v) : 0.0;
+            const int4 *p = reinterpret_cast<const int4 *>(d.rs + row);
+            const int4 s0 = ok ? __ldg(p) : z4, s1 = ok ? __ldg(p + 1) : z4;
+            flip_fp<EQ>(s0, s1, av, up, s, dc);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, VarOut o, int gate)
@@ -389,80 +456,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, Var
         const bool live = q < ncols;
         const int qq = live ? q : 0;
         const int ci0 = __ldg(d.ci_ptr + qq), cf0 = __ldg(d.cf_ptr + qq);
-        const int nI = live ? __ldg(d.ci_ptr + qq + 1) - ci0 : 0;
-        const int nF = live ? __ldg(d.cf_ptr + qq + 1) - cf0 : 0;
+        const int cim = __ldg(d.ci_eq + qq), cfm = __ldg(d.cf_eq + qq);
+        const int ci1 = live ? __ldg(d.ci_ptr + qq + 1) : ci0, cf1 = live ? __ldg(d.cf_ptr + qq + 1) : cf0;
         const int j = __ldg(d.var_list + qq);
         const bool up = __double_as_longlong(d.x[j]) == 0;  // flip 0 -> 1
+        const int nIs = live ? cim - ci0 : 0, nIe = ci1 - (live ? cim : ci1);
+        const int nFs = live ? cfm - cf0 : 0, nFe = cf1 - (live ? cfm : cf1);
         long long s = 0;
         int dc = 0;
-        int nImax = nI, nFmax = nF;
-#pragma unroll
-        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) {
-            nImax = max(nImax, __shfl_xor_sync(FULLMASK, nImax, o2));
-            nFmax = max(nFmax, __shfl_xor_sync(FULLMASK, nFmax, o2));
-        }
-        // integral rows: r1 = r + a (x_j rises) or r - a; the second half of an
-        // "=" row has residual -r and change -(r1 - r)
-        for (int base = 0; base < nImax; base += kBinSlots * kGrp) {
-            int row[kBinSlots], av[kBinSlots];
-#pragma unroll
-            for (int k = 0; k < kBinSlots; ++k) {
-                const int v = base + k * kGrp + sub;
-                const bool ok = v < nI;
-                row[k] = ok ? __ldg(d.ci_row + ci0 + v) : 0;
-                av[k] = ok ? __ldg(d.ci_val + ci0 + v) : 0;
-            }
-            int4 st[kBinSlots];
-#pragma unroll
-            for (int k = 0; k < kBinSlots; ++k) st[k] = av[k] != 0 ? ld_row16(d.rs + row[k]) : make_int4(0, 0, 0, -1);
-#pragma unroll
-            for (int k = 0; k < kBinSlots; ++k) {
-                const long long r = row_r(st[k]);
-                const int ad = up ? av[k] : -av[k];
-                const long long r1 = r + ad;
-                const bool v0 = r > 0, v1 = r1 > 0;
-                s += (long long)flip_f(v0, v1, ad < 0) * st[k].z;
-                dc += (int)v1 - (int)v0;
-                const bool two = st[k].w >= 0;
-                const bool u0 = two && r < 0, u1 = two && r1 < 0;
-                s += (long long)flip_f(u0, u1, ad > 0) * (two ? st[k].w : 0);
-                dc += (int)u1 - (int)u0;
-            }
-        }
-        // non-integral rows: violated <=> m < 0 with m = eps - r of the half;
-        // violated after the move <=> (change of r) > m
-        for (int base = 0; base < nFmax; base += kBinSlots * kGrp) {
-            int row[kBinSlots];
-            double av[kBinSlots];
-            bool ok[kBinSlots];
-#pragma unroll
-            for (int k = 0; k < kBinSlots; ++k) {
-                const int v = base + k * kGrp + sub;
-                ok[k] = v < nF;
-                row[k] = ok[k] ? __ldg(d.cf_row + cf0 + v) : 0;
-                av[k] = ok[k] ? __ldg(d.cf_val + cf0 + v) : 0.0;
-            }
-            int4 s0[kBinSlots], s1[kBinSlots];
-#pragma unroll
-            for (int k = 0; k < kBinSlots; ++k) {
-                const int4 *p = reinterpret_cast<const int4 *>(d.rs + row[k]);
-                s0[k] = ok[k] ? __ldg(p) : make_int4(0, 0, 0, -1);
-                s1[k] = ok[k] ? __ldg(p + 1) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int k = 0; k < kBinSlots; ++k) {
-                const double ad = up ? av[k] : dflip(av[k]);
-                const double m1 = i4_double_lo(s1[k]), m2 = i4_double_hi(s1[k]);
-                const bool neg = dneg(ad);
-                const bool v0 = dneg(m1), v1 = dgt(ad, m1);
-                s += (long long)flip_f(v0, v1, neg) * s0[k].z;
-                dc += (int)v1 - (int)v0;
-                const bool two = s0[k].w >= 0;
-                const bool u0 = two && dneg(m2), u1 = two && dgt(dflip(ad), m2);
-                s += (long long)flip_f(u0, u1, !neg) * (two ? s0[k].w : 0);
-                dc += (int)u1 - (int)u0;
-            }
-        }
+        bin_part<false, false>(d, ci0, nIs, quad_max(nIs), sub, up, s, dc);
+        bin_part<false, true>(d, cim, nIe, quad_max(nIe), sub, up, s, dc);
+        bin_part<true, false>(d, cf0, nFs, quad_max(nFs), sub, up, s, dc);
+        bin_part<true, true>(d, cfm, nFe, quad_max(nFe), sub, up, s, dc);
 #pragma unroll
         for (int o2 = kGrp >> 1; o2 > 0; o2 >>= 1) {
             s += __shfl_xor_sync(FULLMASK, s, o2);
@@ -1026,6 +1031,118 @@ __device__ __noinline__ void column_warp(const Dev &d, const VarOut &o, int q, S
     __syncwarp();
 }
 
+// Classification context of a lane's column (thresholds of the side tests).
+struct NbLane {
+    long long ilo, ihi;          // integer variable: l - xbar, u - xbar
+    float Lp, Ln, Up, Un, tolf;  // float thresholds for a > 0 / a < 0, rounding margin of t
+    bool fok, isint;
+    int g, lane;
+};
+
+struct NbQueue {
+    int head, qn;
+};
+
+// Append the lanes' undecided halves to the warp's ring queue.
+__device__ __forceinline__ void enqueue(NbWarp &W, NbQueue &Q, bool pend, const QItem &it, int lane)
+{
+    const unsigned bal = __ballot_sync(FULLMASK, pend);
+    if (pend) {
+        int pos = Q.head + Q.qn + __popc(bal & ((1u << lane) - 1u));
+        if (pos >= kQCap) pos -= kQCap;
+        W.q[pos] = it;
+    }
+    Q.qn += __popc(bal);
+}
+
+// Exact pass over 32 queued halves while 32 are queued.
+__device__ __forceinline__ void drain(NbWarp &W, NbQueue &Q, int lane)
+{
+    __syncwarp();
+    while (Q.qn >= 32) {
+        flush_queue(W, Q.head, 32, lane);
+        Q.head += 32;
+        if (Q.head >= kQCap) Q.head -= kQCap;
+        Q.qn -= 32;
+    }
+}
+
+// One half of an integral row (integer variable, exact int64 r and a).  Exact
+// side test with z = -r, aa = a (a > 0) or z = r, aa = -a: t < l <=>
+// z <= L' aa - [a > 0] and t > u <=> z > H' aa - [a > 0], where L' = lo,
+// H' = hi + 1 (a > 0) or L' = lo - 1, H' = hi (a < 0); |lo a|, |hi a| <= 2^53
+// on integral rows.
+__device__ __forceinline__ void nb_int_half(long long r, int a, int w, bool act, const NbLane &L, NbWarp &W,
+                                            NbQueue &Q, Acc &acc)
+{
+    const bool V = r > 0, P = a > 0;
+    const long long z = P ? -r : r;
+    const long long aa = P ? a : -a;
+    const long long Lz = (P ? L.ilo : L.ilo - 1) * aa - (long long)P;
+    const long long Rz = (P ? L.ihi + 1 : L.ihi) * aa - (long long)P;
+    const bool left = z <= Lz, right = z > Rz;
+    const bool dec = act && (left || right);
+    acc_decided(dec ? (((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
+    enqueue(W, Q, act && !dec, QItem{r, (long long)a, w, L.g | ((int)V << 3)}, L.lane);
+}
+
+template <bool EQ>
+__device__ __forceinline__ void nb_int_part(const Dev &d, int e0, int n, int nmax, int sub, const NbLane &L,
+                                            NbWarp &W, NbQueue &Q, Acc &acc)
+{
+    for (int base = 0; base < nmax; base += kGrp) {
+        const int v = base + sub;
+        const bool ok = v < n;
+        const int row = ok ? __ldg(d.ci_row + e0 + v) : 0;
+        const int av = ok ? __ldg(d.ci_val + e0 + v) : 1;
+        const int4 st = ok ? ld_row16(d.rs + row) : make_int4(0, 0, 0, 0);
+        const long long r = row_r(st);
+        nb_int_half(r, av, st.z, ok, L, W, Q, acc);
+        if (EQ) nb_int_half(-r, -av, st.w, ok, L, W, Q, acc);
+        drain(W, Q, L.lane);
+    }
+}
+
+// One half of a non-integral row: residual r, coefficient a, margins m = eps - r
+// of the half and mo of the other half.  Integer variable: z = m; continuous:
+// z = -r; the breakpoint is placed by float products with margins, and
+// |r| <= eps makes the half tight wherever t is.
+__device__ __forceinline__ void nb_fp_half(double r, double a, double m, double mo, int w, bool act,
+                                           const NbLane &L, NbWarp &W, NbQueue &Q, Acc &acc)
+{
+    const bool V = dneg(m), P = !dneg(a);
+    const bool T = !L.isint && !V && !dneg(mo);
+    const double z0 = L.isint ? m : dflip(r);
+    bool fin = L.fok;
+    const float zf = approx_f(P ? z0 : dflip(z0), fin), af = approx_f(P ? a : dflip(a), fin);
+    bool left = false, right = false;
+    if (fin) side_test(zf, af, P ? L.Lp : L.Ln, P ? L.Up : L.Un, L.tolf * af, left, right);
+    const bool dec = act && (T || left || right);
+    acc_decided(dec ? (((int)T << 3) | ((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
+    enqueue(W, Q, act && !dec,
+            QItem{__double_as_longlong(L.isint ? m : r), __double_as_longlong(a), w, L.g | 4 | ((int)V << 3)},
+            L.lane);
+}
+
+template <bool EQ>
+__device__ __forceinline__ void nb_fp_part(const Dev &d, int e0, int n, int nmax, int sub, const NbLane &L,
+                                           NbWarp &W, NbQueue &Q, Acc &acc)
+{
+    for (int base = 0; base < nmax; base += kGrp) {
+        const int v = base + sub;
+        const bool ok = v < n;
+        const int row = ok ? __ldg(d.cf_row + e0 + v) : 0;
+        const double a = ok ? __ldg(d.cf_val + e0 + v) : 1.0;
+        const int4 *p = reinterpret_cast<const int4 *>(d.rs + row);
+        const int4 s0 = ok ? __ldg(p) : make_int4(0, 0, 0, 0);
+        const int4 s1 = ok ? __ldg(p + 1) : make_int4(0, 0, 0, 0);
+        const double r = i4_double_lo(s0), m1 = i4_double_lo(s1), m2 = i4_double_hi(s1);
+        nb_fp_half(r, a, m1, m2, s0.z, ok, L, W, Q, acc);
+        if (EQ) nb_fp_half(dflip(r), dflip(a), m2, m1, s0.w, ok, L, W, Q, acc);
+        drain(W, Q, L.lane);
+    }
+}
+
 __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int ncols, VarOut o, int slot0, int gate)
 {
     if (gated_done(d, gate)) return;
@@ -1076,127 +1193,16 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
             }
         }
         __syncwarp();
-        int head = 0, qn = 0;
+        NbQueue Q{0, 0};
         Acc acc{0, 0, 0, 0};
-        int nImax = nI, nFmax = nv - nI;
-#pragma unroll
-        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) {
-            nImax = max(nImax, __shfl_xor_sync(FULLMASK, nImax, o2));
-            nFmax = max(nFmax, __shfl_xor_sync(FULLMASK, nFmax, o2));
-        }
-        // integral rows (integer variables only): exact int64 r and a
-        for (int base = 0; base < nImax; base += kNbSlots * kGrp) {
-            int row[kNbSlots], av[kNbSlots];
-            bool ok[kNbSlots];
-#pragma unroll
-            for (int k = 0; k < kNbSlots; ++k) {
-                const int v = base + k * kGrp + sub;
-                ok[k] = v < nI;
-                row[k] = ok[k] ? __ldg(d.ci_row + ci0 + v) : 0;
-                av[k] = ok[k] ? __ldg(d.ci_val + ci0 + v) : 1;
-            }
-            int4 s0[kNbSlots];
-#pragma unroll
-            for (int k = 0; k < kNbSlots; ++k) s0[k] = ok[k] ? ld_row16(d.rs + row[k]) : make_int4(0, 0, 0, -1);
-#pragma unroll
-            for (int k = 0; k < kNbSlots; ++k) {
-                const long long r1 = row_r(s0[k]);
-#pragma unroll
-                for (int hf = 0; hf < 2; ++hf) {
-                    const bool act = ok[k] && (hf == 0 || s0[k].w >= 0);
-                    if (hf == 1 && !__any_sync(FULLMASK, act)) continue;
-                    const long long r = hf ? -r1 : r1;
-                    const int a = hf ? -av[k] : av[k];
-                    const int w = hf ? s0[k].w : s0[k].z;
-                    const bool V = r > 0, P = a > 0;
-                    // exact side test with z = -r, aa = a (a > 0) or z = r, aa = -a:
-                    // t < l <=> z <= L' aa - [a > 0], t > u <=> z > H' aa - [a > 0] with
-                    // L' = lo, H' = hi + 1 (a > 0) or L' = lo - 1, H' = hi (a < 0);
-                    // |lo a|, |hi a| <= 2^53 on integral rows
-                    const long long z = P ? -r : r;
-                    const long long aa = P ? a : -a;
-                    const long long Lz = (P ? ilo : ilo - 1) * aa - (long long)P;
-                    const long long Rz = (P ? ihi + 1 : ihi) * aa - (long long)P;
-                    const bool left = z <= Lz, right = z > Rz;
-                    const bool dec = act && (left || right);
-                    acc_decided(dec ? (((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
-                    const bool pend = act && !dec;
-                    const unsigned bal = __ballot_sync(FULLMASK, pend);
-                    if (pend) {
-                        int pos = head + qn + __popc(bal & ((1u << lane) - 1u));
-                        if (pos >= kQCap) pos -= kQCap;
-                        W.q[pos] = QItem{r, (long long)a, w, g | ((int)V << 3)};
-                    }
-                    qn += __popc(bal);
-                }
-            }
-            __syncwarp();
-            while (qn >= 32) {
-                flush_queue(W, head, 32, lane);
-                head += 32;
-                if (head >= kQCap) head -= kQCap;
-                qn -= 32;
-            }
-        }
-        // non-integral rows: margins m = eps - r, mo = eps + r of the half
-        for (int base = 0; base < nFmax; base += kNbSlots * kGrp) {
-            int row[kNbSlots];
-            double av[kNbSlots];
-            bool ok[kNbSlots];
-#pragma unroll
-            for (int k = 0; k < kNbSlots; ++k) {
-                const int v = nI + base + k * kGrp + sub;
-                ok[k] = v < nv;
-                row[k] = ok[k] ? __ldg(d.cf_row + cf0 + (v - nI)) : 0;
-                av[k] = ok[k] ? __ldg(d.cf_val + cf0 + (v - nI)) : 1.0;
-            }
-            int4 s0[kNbSlots], s1[kNbSlots];
-#pragma unroll
-            for (int k = 0; k < kNbSlots; ++k) {
-                const int4 *p = reinterpret_cast<const int4 *>(d.rs + row[k]);
-                s0[k] = ok[k] ? __ldg(p) : make_int4(0, 0, 0, -1);
-                s1[k] = ok[k] ? __ldg(p + 1) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int k = 0; k < kNbSlots; ++k) {
-#pragma unroll
-                for (int hf = 0; hf < 2; ++hf) {
-                    const bool act = ok[k] && (hf == 0 || s0[k].w >= 0);
-                    if (hf == 1 && !__any_sync(FULLMASK, act)) continue;
-                    const double r0 = i4_double_lo(s0[k]);
-                    const double r = hf ? dflip(r0) : r0, a = hf ? dflip(av[k]) : av[k];
-                    const double m = hf ? i4_double_hi(s1[k]) : i4_double_lo(s1[k]);
-                    const double mo = hf ? i4_double_lo(s1[k]) : i4_double_hi(s1[k]);
-                    const int w = hf ? s0[k].w : s0[k].z;
-                    const bool V = dneg(m), P = !dneg(a);
-                    const bool T = !isint && !V && !dneg(mo);  // |r| <= eps: tight wherever t is
-                    // z = m (integer variable) or -r (continuous); a > 0 after flipping both
-                    const double z0 = isint ? m : dflip(r);
-                    bool fin = fok;
-                    const float zf = approx_f(P ? z0 : dflip(z0), fin), af = approx_f(P ? a : dflip(a), fin);
-                    bool left = false, right = false;
-                    if (fin) side_test(zf, af, P ? Lp : Ln, P ? Up : Un, tolf * af, left, right);
-                    const bool dec = act && (T || left || right);
-                    acc_decided(dec ? (((int)T << 3) | ((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
-                    const bool pend = act && !dec;
-                    const unsigned bal = __ballot_sync(FULLMASK, pend);
-                    if (pend) {
-                        int pos = head + qn + __popc(bal & ((1u << lane) - 1u));
-                        if (pos >= kQCap) pos -= kQCap;
-                        W.q[pos] = QItem{__double_as_longlong(isint ? m : r), __double_as_longlong(a), w,
-                                         g | 4 | ((int)V << 3)};
-                    }
-                    qn += __popc(bal);
-                }
-            }
-            __syncwarp();
-            while (qn >= 32) {
-                flush_queue(W, head, 32, lane);
-                head += 32;
-                if (head >= kQCap) head -= kQCap;
-                qn -= 32;
-            }
-        }
+        const NbLane L{ilo, ihi, Lp, Ln, Up, Un, tolf, fok, isint, g, lane};
+        const int cim = live ? __ldg(d.ci_eq + q0 + cq) : ci0, cfm = live ? __ldg(d.cf_eq + q0 + cq) : cf0;
+        const int nIs = cim - ci0, nIe = nI - nIs, nFs = cfm - cf0, nFe = (nv - nI) - nFs;
+        nb_int_part<false>(d, ci0, nIs, quad_max(nIs), sub, L, W, Q, acc);
+        nb_int_part<true>(d, cim, nIe, quad_max(nIe), sub, L, W, Q, acc);
+        nb_fp_part<false>(d, cf0, nFs, quad_max(nFs), sub, L, W, Q, acc);
+        nb_fp_part<true>(d, cfm, nFe, quad_max(nFe), sub, L, W, Q, acc);
+        const int head = Q.head, qn = Q.qn;
         if (qn > 0) flush_queue(W, head, qn, lane);
         // group sums of the scalars
 #pragma unroll
