@@ -135,7 +135,11 @@ typedef struct chap_info {
     int32_t eval_blocks;      /* CTAs of one best-shift pass */
     int32_t n_hist_cols;      /* columns on the multi-CTA histogram path */
     int32_t launches_per_step;/* kernel launches of one tabu iteration (chap_bs_step) */
-    int32_t reserved[7];
+    int32_t grid_bin;         /* CTAs of the persistent binary-flip kernel (0: no binary column) */
+    int32_t grid_nb;          /* CTAs of the persistent short-column kernel (0: none) */
+    int64_t bytes_bin;        /* algorithmic bytes of one launch of the binary-flip kernel */
+    int64_t bytes_nb;         /* algorithmic bytes of one launch of the short-column kernel */
+    int32_t reserved[2];
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);
@@ -158,6 +162,20 @@ CHAP_API chap_status chap_bs_create(const chap_problem *prob, const chap_options
 CHAP_API chap_status chap_bs_destroy(struct chap_bs *h);
 
 CHAP_API chap_status chap_bs_info(const struct chap_bs *h, chap_info *info);
+
+/*
+ * Kernel timing (measurement aid; no counterpart in the paper).  With
+ * enable != 0 the following chap_bs_best_shift / chap_bs_step calls record CUDA
+ * events on each kernel's own stream around every evaluation kernel and the
+ * selection (never inside chap_tabu_run's graph).  chap_bs_kernel_ms then
+ * synchronises the handle's stream and writes the durations of the last
+ * profiled pass in milliseconds: ms[0] binary flips, ms[1] short non-binary
+ * columns, ms[2] CTA-sorted columns, ms[3] counting-sorted columns, ms[4]
+ * selection (0 for a kernel the instance does not launch).  ms has 5
+ * elements (host).  CHAP_E_STATE when no profiled pass ran since enabling.
+ */
+CHAP_API chap_status chap_bs_profile(struct chap_bs *h, int32_t enable);
+CHAP_API chap_status chap_bs_kernel_ms(struct chap_bs *h, float *ms);
 
 /*
  * Set the assignment and weights, reset tabu stamps and the iteration counter

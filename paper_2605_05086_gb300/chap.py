@@ -24,6 +24,7 @@ EXPORTED = [
     "chap_options_default", "chap_bs_create", "chap_bs_destroy", "chap_bs_info", "chap_bs_set_state",
     "chap_bs_set_checkpoint", "chap_bs_get_state", "chap_bs_residuals", "chap_bs_best_shift",
     "chap_bs_apply", "chap_bs_step", "chap_tabu_run", "chap_status_str", "chap_last_error",
+    "chap_bs_profile", "chap_bs_kernel_ms",
 ]
 
 
@@ -62,7 +63,8 @@ class chap_info(C.Structure):
                 ("n_bin", C.c_int32), ("n_int", C.c_int32), ("n_cont", C.c_int32), ("n_fixed", C.c_int32),
                 ("nnz", C.c_int64), ("nnz_int_rows", C.c_int64), ("nnz_fp_rows", C.c_int64),
                 ("bytes_per_pass", C.c_int64), ("eval_blocks", C.c_int32), ("n_hist_cols", C.c_int32),
-                ("launches_per_step", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("launches_per_step", C.c_int32), ("grid_bin", C.c_int32), ("grid_nb", C.c_int32),
+                ("bytes_bin", C.c_int64), ("bytes_nb", C.c_int64), ("reserved", C.c_int32 * 2)]
 
 
 _lib = None
@@ -98,6 +100,8 @@ def load(build_if_missing: bool = True):
         "chap_tabu_run": (I32, [P, P, P]),
         "chap_status_str": (C.c_char_p, [I32]),
         "chap_last_error": (C.c_char_p, [P]),
+        "chap_bs_profile": (I32, [P, I32]),
+        "chap_bs_kernel_ms": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +194,18 @@ def chap_bs_get_state(h, n, m_norm):
     _check(h, load().chap_bs_get_state(h, _ptr(x), _ptr(w), _ptr(ti), _ptr(td), _ptr(sc), CHAP_MEM_HOST))
     return dict(x=x, w=w, tabu_inc=ti, tabu_dec=td, iter=int(sc[0]), nviol=int(sc[1]),
                 best_nviol=int(sc[2]), feasible_iter=int(sc[3]), moves=int(sc[4]), weight_updates=int(sc[5]))
+
+
+def chap_bs_profile(h, enable=True):
+    _check(h, load().chap_bs_profile(h, 1 if enable else 0))
+
+
+def chap_bs_kernel_ms(h):
+    """Durations (ms) of the kernels of the last profiled pass: binary flips,
+    short columns, CTA sort, counting sort, selection."""
+    ms = np.zeros(5, np.float32)
+    _check(h, load().chap_bs_kernel_ms(h, _ptr(ms)))
+    return ms
 
 
 def chap_bs_residuals(h, m_norm, out=None, mem=CHAP_MEM_HOST):

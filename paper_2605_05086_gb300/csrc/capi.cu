@@ -40,6 +40,7 @@ struct chap_bs {
     cudaGraphExec_t gexec = nullptr;
     int g_iters = 0;
     bool broken = false;
+    bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
     std::string err;
 };
 
@@ -164,6 +165,8 @@ void free_all(chap_bs *h)
         if (h->plan.ev_join[k]) { cudaEventDestroy(h->plan.ev_join[k]); h->plan.ev_join[k] = nullptr; }
     }
     if (h->plan.ev_fork) { cudaEventDestroy(h->plan.ev_fork); h->plan.ev_fork = nullptr; }
+    for (int k = 0; k < 10; ++k)
+        if (h->plan.pev[k]) { cudaEventDestroy(h->plan.pev[k]); h->plan.pev[k] = nullptr; }
 }
 
 chap_status read_ctl(chap_bs *h)
@@ -515,6 +518,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         if (cudaStreamCreateWithFlags(&h->plan.side[k], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&h->plan.ev_join[k], cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); ok = false; }
     if (ok && cudaEventCreateWithFlags(&h->plan.ev_fork, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); ok = false; }
+    for (int k = 0; k < 10 && ok; ++k)
+        if (cudaEventCreate(&h->plan.pev[k]) != cudaSuccess) { cudaGetLastError(); ok = false; }
     if (!ok) {
         free_all(h);
         delete h;
@@ -575,6 +580,25 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     int64_t n_act = n - n_fixed;
     in.bytes_per_pass = 8 * nnz_int + 12 * (p->nnz - nnz_int) + 16LL * (m - m_fp) + 32LL * m_fp +
                         n_act * (8 /*x*/ + 8 /*column pointers*/ + 8 /*tabu*/ + 1 /*type*/) + nb_bytes_vars;
+    // algorithmic bytes of one launch of the binary and short-column kernels:
+    // their nonzeros (row + coefficient), the state of every row they touch
+    // once, and per column its position entry, x, four part offsets and, for
+    // the short columns, the bounds, the type and the two tabu stamps
+    {
+        auto kernel_bytes = [&](int q0, int q1, int64_t per_col) {
+            std::vector<char> touched(m, 0);
+            int64_t b = 8LL * (ci_ptr[q1] - ci_ptr[q0]) + 12LL * (cf_ptr[q1] - cf_ptr[q0]);
+            for (int e = ci_ptr[q0]; e < ci_ptr[q1]; ++e) touched[ci_row[e]] = 1;
+            for (int e = cf_ptr[q0]; e < cf_ptr[q1]; ++e) touched[cf_row[e]] = 1;
+            for (int i = 0; i < m; ++i)
+                if (touched[i]) b += rint[i] ? 16 : 32;
+            return b + per_col * (q1 - q0);
+        };
+        in.grid_bin = n_tb;
+        in.grid_nb = n_tn;
+        in.bytes_bin = bin_cols ? kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16) : 0;
+        in.bytes_nb = nb_cols ? kernel_bytes(kind_base[T_NB], kind_base[T_NB + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;
+    }
 
     std::vector<double> x0(n);
     for (int j = 0; j < n; ++j) x0[j] = std::min(std::max(0.0, h->lb[j]), h->ub[j]);
@@ -593,6 +617,28 @@ chap_status chap_bs_info(const chap_bs *h, chap_info *info)
 {
     if (!h || !info) return CHAP_E_INVALID;
     *info = h->info;
+    return CHAP_OK;
+}
+
+chap_status chap_bs_profile(chap_bs *h, int32_t enable)
+{
+    if (!h) return CHAP_E_INVALID;
+    h->plan.profile = enable != 0;
+    h->prof_valid = false;
+    return CHAP_OK;
+}
+
+chap_status chap_bs_kernel_ms(chap_bs *h, float *ms)
+{
+    if (!h || !ms) return CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (!h->prof_valid) return fail(h, CHAP_E_STATE, "no profiled pass since chap_bs_profile(h, 1)");
+    CK(h, cudaStreamSynchronize(h->st), "synchronise");
+    const bool launched[5] = {h->plan.n_bin > 0, h->plan.nb_grid > 0, h->plan.n_cta > 0, h->plan.n_hist_tiles > 0, true};
+    for (int k = 0; k < 5; ++k) {
+        ms[k] = 0.0f;
+        if (launched[k]) CK(h, cudaEventElapsedTime(&ms[k], h->plan.pev[2 * k], h->plan.pev[2 * k + 1]), "kernel timing");
+    }
     return CHAP_OK;
 }
 
@@ -693,7 +739,8 @@ chap_status chap_bs_best_shift(chap_bs *h, double *xhat, int64_t *score_half, in
     if (score_half) o.s = host ? h->t_s : reinterpret_cast<long long *>(score_half);
     if (dnviol) o.dc = host ? h->t_dc : dnviol;
     CK(h, launch_eval_gated(h->dev, h->plan, o, 0, h->st), "best-shift kernels");
-    CK(h, launch_select_gated(h->dev, 0, h->st), "selection kernel");
+    CK(h, launch_select_gated(h->dev, h->plan, 0, h->st), "selection kernel");
+    if (h->plan.profile) h->prof_valid = true;
     if (host && h->n) {
         if (xhat) CK(h, cudaMemcpyAsync(xhat, h->t_xhat, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st), "copy xhat");
         if (score_half) CK(h, cudaMemcpyAsync(score_half, h->t_s, sizeof(long long) * h->n, cudaMemcpyDeviceToHost, h->st), "copy scores");
@@ -735,7 +782,8 @@ chap_status chap_bs_step(chap_bs *h, chap_move *out)
     if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
     VarOut o{nullptr, nullptr, nullptr};
     CK(h, launch_eval_gated(h->dev, h->plan, o, 0, h->st), "best-shift kernels");
-    CK(h, launch_select_gated(h->dev, 0, h->st), "selection kernel");
+    CK(h, launch_select_gated(h->dev, h->plan, 0, h->st), "selection kernel");
+    if (h->plan.profile) h->prof_valid = true;
     CK(h, launch_apply_gated(h->dev, h->plan, 0, h->st), "apply kernel");
     if (out) {
         chap_status s = read_ctl(h);
@@ -774,7 +822,7 @@ chap_status chap_tabu_run(chap_bs *h, const chap_options *opts, chap_tabu_result
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < o.graph_iters && e == cudaSuccess; ++k) {
             e = launch_eval_gated(d, h->plan, none, 1, h->cap_st);
-            if (e == cudaSuccess) e = launch_select_gated(d, 1, h->cap_st);
+            if (e == cudaSuccess) e = launch_select_gated(d, h->plan, 1, h->cap_st);
             if (e == cudaSuccess) e = launch_apply_gated(d, h->plan, 1, h->cap_st);
         }
         cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &g);

@@ -188,6 +188,11 @@ struct LaunchPlan {
     int apply_blocks;
     cudaStream_t side[3];      // side streams of the non-binary evaluation kernels
     cudaEvent_t ev_fork, ev_join[3];
+    // optional timing of the kernels of one pass (outside graph capture):
+    // pev[2k], pev[2k+1] around evaluation kernel k (bin, nb, cta, hist) on its
+    // stream, pev[8], pev[9] around the selection
+    int profile;
+    cudaEvent_t pev[10];
 };
 
 // Kernel launchers (kernels.cu).  All are asynchronous on `st`; `gate` makes a
@@ -196,7 +201,7 @@ cudaError_t setup_kernel_attributes(const LaunchPlan &p);
 int bin_grid_size(int ncols);  // persistent grids of the binary and short-column kernels on the current device
 int nb_grid_size(int ncols);
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
-cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st);
+cudaError_t launch_select_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
 cudaError_t launch_set_move(const Dev &d, int var, double new_value, cudaStream_t st);
 cudaError_t launch_residuals(const Dev &d, cudaStream_t st);

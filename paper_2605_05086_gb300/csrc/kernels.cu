@@ -33,6 +33,7 @@
 #include "chap_internal.h"
 
 #include <climits>
+#include <type_traits>
 #include <cstdint>
 
 namespace chap {
@@ -421,25 +422,37 @@ __device__ __forceinline__ void flip_fp(const int4 &s0, const int4 &s1, double a
 }
 
 // Flip scores of one part of a column (FP: non-integral rows; EQ: "=" rows,
-// both halves), one nonzero per lane and round.
+// both halves), one nonzero per lane and round.  The row index and
+// coefficient of the next round are loaded while the current round's row
+// state is gathered, so a round waits for one memory latency, not two.
 template <bool FP, bool EQ>
 __device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, int sub, bool up, long long &s, int &dc)
 {
+    using Val = typename std::conditional<FP, double, int>::type;
+    const int *rowp = (FP ? d.cf_row : d.ci_row) + e0;
+    const Val *valp = reinterpret_cast<const Val *>(FP ? (const void *)d.cf_val : (const void *)d.ci_val) + e0;
+    bool ok = sub < n;
+    int row = ok ? __ldg(rowp + sub) : 0;
+    Val av = ok ? __ldg(valp + sub) : Val(0);
+    const int4 z4 = make_int4(0, 0, 0, 0);
     for (int base = 0; base < nmax; base += kGrp) {
-        const int v = base + sub;
-        const bool ok = v < n;
-        const int row = ok ? __ldg((FP ? d.cf_row : d.ci_row) + e0 + v) : 0;
-        const int4 z4 = make_int4(0, 0, 0, 0);
+        int4 s0, s1 = z4;
         if (!FP) {
-            const int av = ok ? __ldg(d.ci_val + e0 + v) : 0;
-            const int4 st = ok ? ld_row16(d.rs + row) : z4;
-            flip_int<EQ>(st, av, up, s, dc);
+            s0 = ok ? ld_row16(d.rs + row) : z4;
         } else {
-            const double av = ok ? __ldg(d.cf_val + e0 + v) : 0.0;
             const int4 *p = reinterpret_cast<const int4 *>(d.rs + row);
-            const int4 s0 = ok ? __ldg(p) : z4, s1 = ok ? __ldg(p + 1) : z4;
-            flip_fp<EQ>(s0, s1, av, up, s, dc);
+            s0 = ok ? __ldg(p) : z4;
+            s1 = ok ? __ldg(p + 1) : z4;
         }
+        const int vn = base + kGrp + sub;
+        const bool okn = vn < n;
+        const int rown = okn ? __ldg(rowp + vn) : 0;
+        const Val avn = okn ? __ldg(valp + vn) : Val(0);
+        if (!FP) flip_int<EQ>(s0, (int)av, up, s, dc);
+        else flip_fp<EQ>(s0, s1, (double)av, up, s, dc);
+        ok = okn;
+        row = rown;
+        av = avn;
     }
 }
 
@@ -1086,20 +1099,29 @@ __device__ __forceinline__ void nb_int_half(long long r, int a, int w, bool act,
     enqueue(W, Q, act && !dec, QItem{r, (long long)a, w, L.g | ((int)V << 3)}, L.lane);
 }
 
+// Both loops below load the next round's row index and coefficient while the
+// current round's row state is gathered (one memory latency per round).
 template <bool EQ>
 __device__ __forceinline__ void nb_int_part(const Dev &d, int e0, int n, int nmax, int sub, const NbLane &L,
                                             NbWarp &W, NbQueue &Q, Acc &acc)
 {
+    const int *rowp = d.ci_row + e0, *valp = d.ci_val + e0;
+    bool ok = sub < n;
+    int row = ok ? __ldg(rowp + sub) : 0;
+    int av = ok ? __ldg(valp + sub) : 1;
     for (int base = 0; base < nmax; base += kGrp) {
-        const int v = base + sub;
-        const bool ok = v < n;
-        const int row = ok ? __ldg(d.ci_row + e0 + v) : 0;
-        const int av = ok ? __ldg(d.ci_val + e0 + v) : 1;
         const int4 st = ok ? ld_row16(d.rs + row) : make_int4(0, 0, 0, 0);
+        const int vn = base + kGrp + sub;
+        const bool okn = vn < n;
+        const int rown = okn ? __ldg(rowp + vn) : 0;
+        const int avn = okn ? __ldg(valp + vn) : 1;
         const long long r = row_r(st);
         nb_int_half(r, av, st.z, ok, L, W, Q, acc);
         if (EQ) nb_int_half(-r, -av, st.w, ok, L, W, Q, acc);
         drain(W, Q, L.lane);
+        ok = okn;
+        row = rown;
+        av = avn;
     }
 }
 
@@ -1128,18 +1150,26 @@ template <bool EQ>
 __device__ __forceinline__ void nb_fp_part(const Dev &d, int e0, int n, int nmax, int sub, const NbLane &L,
                                            NbWarp &W, NbQueue &Q, Acc &acc)
 {
+    const int *rowp = d.cf_row + e0;
+    const double *valp = d.cf_val + e0;
+    bool ok = sub < n;
+    int row = ok ? __ldg(rowp + sub) : 0;
+    double a = ok ? __ldg(valp + sub) : 1.0;
     for (int base = 0; base < nmax; base += kGrp) {
-        const int v = base + sub;
-        const bool ok = v < n;
-        const int row = ok ? __ldg(d.cf_row + e0 + v) : 0;
-        const double a = ok ? __ldg(d.cf_val + e0 + v) : 1.0;
         const int4 *p = reinterpret_cast<const int4 *>(d.rs + row);
         const int4 s0 = ok ? __ldg(p) : make_int4(0, 0, 0, 0);
         const int4 s1 = ok ? __ldg(p + 1) : make_int4(0, 0, 0, 0);
+        const int vn = base + kGrp + sub;
+        const bool okn = vn < n;
+        const int rown = okn ? __ldg(rowp + vn) : 0;
+        const double an = okn ? __ldg(valp + vn) : 1.0;
         const double r = i4_double_lo(s0), m1 = i4_double_lo(s1), m2 = i4_double_hi(s1);
         nb_fp_half(r, a, m1, m2, s0.z, ok, L, W, Q, acc);
         if (EQ) nb_fp_half(dflip(r), dflip(a), m2, m1, s0.w, ok, L, W, Q, acc);
         drain(W, Q, L.lane);
+        ok = okn;
+        row = rown;
+        a = an;
     }
 }
 
@@ -1796,11 +1826,31 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (side[k]) e = cudaStreamWaitEvent(p.side[k], p.ev_fork, 0);
     if (e != cudaSuccess) return e;
-    if (p.n_bin) k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate);
-    if (p.nb_grid) k_eval_nb<<<p.nb_grid, kEvalThreads, kNbSmem, p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
-    if (p.n_cta) k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
-    if (p.n_hist_tiles) k_eval_hist<<<p.n_hist_tiles, kHistThreads, p.hist_smem, p.side[2]>>>(d, p.tiles_hist, o, gate);
-    e = cudaGetLastError();
+    const bool prof = p.profile && !gate;
+    const cudaStream_t ks[4] = {st, p.side[0], p.side[1], p.side[2]};
+#define PROF(k, i) if (prof && e == cudaSuccess) e = cudaEventRecord(p.pev[2 * (k) + (i)], ks[k])
+    if (p.n_bin) {
+        PROF(0, 0);
+        k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate);
+        PROF(0, 1);
+    }
+    if (p.nb_grid) {
+        PROF(1, 0);
+        k_eval_nb<<<p.nb_grid, kEvalThreads, kNbSmem, p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
+        PROF(1, 1);
+    }
+    if (p.n_cta) {
+        PROF(2, 0);
+        k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
+        PROF(2, 1);
+    }
+    if (p.n_hist_tiles) {
+        PROF(3, 0);
+        k_eval_hist<<<p.n_hist_tiles, kHistThreads, p.hist_smem, p.side[2]>>>(d, p.tiles_hist, o, gate);
+        PROF(3, 1);
+    }
+#undef PROF
+    if (e == cudaSuccess) e = cudaGetLastError();
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
         if (!side[k]) continue;
         e = cudaEventRecord(p.ev_join[k], p.side[k]);
@@ -1809,10 +1859,15 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     return e;
 }
 
-cudaError_t launch_select_gated(const Dev &d, int gate, cudaStream_t st)
+cudaError_t launch_select_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st)
 {
+    const bool prof = p.profile && !gate;
+    cudaError_t e = prof ? cudaEventRecord(p.pev[8], st) : cudaSuccess;
+    if (e != cudaSuccess) return e;
     k_select<<<1, 1024, 0, st>>>(d, gate);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && prof) e = cudaEventRecord(p.pev[9], st);
+    return e;
 }
 
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st)

@@ -283,3 +283,54 @@ def test_long_continuous_column_cta_path(chap):
     bs.set_state(x0)
     st = bs.state()
     assert_exact(bs.best_shift()[:3], oracle_pass(orc, st))
+
+
+def _breakpoint_columns(seed, lengths, dom=200, eq_frac=0.2):
+    """Integer columns j with lengths[j] single-variable rows each, whose
+    breakpoints lie inside [0, dom]: every row contributes an entry to the
+    column's list, so the lists have about lengths[j] entries (short lists,
+    8/16/32-entry group sorts, lists longer than a group holds)."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals, rhs, sense = [], [], [], [], []
+    i = 0
+    for j, L in enumerate(lengths):
+        for _ in range(L):
+            a = int(rng.choice([1, 2, 3, -1, -2]))
+            t = int(rng.integers(0, dom + 1))
+            s = int(rng.choice([0, 1, 2], p=[(1 - eq_frac) / 2, (1 - eq_frac) / 2, eq_frac]))
+            rows.append(i); cols.append(j); vals.append(float(a))
+            rhs.append(float(a * t + int(rng.integers(-1, 2))))
+            sense.append(s)
+            i += 1
+    n, m = len(lengths), i
+    vt = np.full(n, inst.VAR_INT)
+    return inst.from_triplets(f"bp_columns_{seed}", n, m, rows, cols, vals, np.zeros(n), np.full(n, float(dom)),
+                              np.ones(n), np.array(rhs), vt, np.array(sense, dtype=np.uint8), x0=np.zeros(n))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_list_lengths_group_and_warp_paths(chap, seed):
+    """Columns whose lists take every sort of the short-column kernel (8, 16 and
+    32 entries per group, the whole-warp path for lists longer than a group
+    holds) and the counting sort, plus a partial last column quadruple."""
+    prob = _breakpoint_columns(seed, [3, 7, 12, 20, 30, 45, 60, 100, 5])
+    orc = Oracle(prob)
+    bs = chap.BestShift(prob, tenure=3)
+    for it in range(4):
+        st = bs.state()
+        assert_exact(bs.best_shift()[:3], oracle_pass(orc, st))
+        bs.run(max_iters=7, stop_at_feasible=0)
+
+
+def test_kernel_timing_api(chap, general_small):
+    bs = chap.BestShift(general_small, tenure=10)
+    with pytest.raises(chap.ChapError):
+        chap.chap_bs_kernel_ms(bs.h)
+    chap.chap_bs_profile(bs.h, True)
+    bs.best_shift()
+    ms = chap.chap_bs_kernel_ms(bs.h)
+    info = bs.info
+    assert ms[0] > 0 and ms[1] > 0 and ms[4] > 0
+    assert info.grid_bin > 0 and info.grid_nb > 0 and info.bytes_bin > 0 and info.bytes_nb > 0
+    chap.chap_bs_profile(bs.h, False)
+    bs.close()
