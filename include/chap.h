@@ -235,6 +235,23 @@ CHAP_API chap_status chap_bs_best_shift(struct chap_bs *h, double *xhat, int64_t
  */
 CHAP_API chap_status chap_bs_apply(struct chap_bs *h, int32_t var, double new_value);
 
+/*
+ * Same pass and outputs as chap_bs_best_shift, but the long integer columns
+ * sorted by the multi-CTA counting sort use a fixed scratch compiled into the
+ * library (a file-scope device array: 65536 bins, 256 columns) instead of the
+ * handle's own scratch.  No counterpart in the paper: it is for callers that
+ * must not hold device memory per handle for this scratch (many handles under
+ * a fixed device-memory budget).  The call allocates nothing; the first call
+ * on a device resolves the scratch's address (do it before any stream
+ * capture).  The scratch starts at zero and every pass leaves it at zero; it is
+ * shared by all handles of the process, so passes through it must not overlap
+ * (same or different handles, any streams): overlapping calls race.
+ * CHAP_E_UNSUPPORTED (with a message) when the instance needs more than 65536
+ * bins or 256 columns.  Arguments as chap_bs_best_shift.
+ */
+CHAP_API chap_status chap_bs_best_shift_static_scratch(struct chap_bs *h, double *xhat, int64_t *score_half,
+                                                       int32_t *dnviol, chap_move *best, int32_t mem);
+
 /* One full tabu iteration: best-shift pass, selection, then apply or weight update.
  * out (host, optional) receives the move taken. */
 CHAP_API chap_status chap_bs_step(struct chap_bs *h, chap_move *out);

@@ -24,7 +24,7 @@ EXPORTED = [
     "chap_options_default", "chap_bs_create", "chap_bs_destroy", "chap_bs_info", "chap_bs_set_state",
     "chap_bs_set_checkpoint", "chap_bs_get_state", "chap_bs_residuals", "chap_bs_best_shift",
     "chap_bs_apply", "chap_bs_step", "chap_tabu_run", "chap_status_str", "chap_last_error",
-    "chap_bs_profile", "chap_bs_kernel_ms",
+    "chap_bs_profile", "chap_bs_kernel_ms", "chap_bs_best_shift_static_scratch",
 ]
 
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         "chap_last_error": (C.c_char_p, [P]),
         "chap_bs_profile": (I32, [P, I32]),
         "chap_bs_kernel_ms": (I32, [P, P]),
+        "chap_bs_best_shift_static_scratch": (I32, [P, P, P, P, P, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -222,6 +223,19 @@ def chap_bs_best_shift(h, n=None, xhat=None, score_half=None, dnviol=None, mem=C
         dnviol = np.zeros(n, np.int32)
     mv = chap_move()
     _check(h, load().chap_bs_best_shift(h, _ptr(xhat), _ptr(score_half), _ptr(dnviol), C.byref(mv), mem))
+    return xhat, score_half, dnviol, mv
+
+
+def chap_bs_best_shift_static_scratch(h, n=None, xhat=None, score_half=None, dnviol=None, mem=CHAP_MEM_HOST,
+                                      want_vars=True):
+    """chap_bs_best_shift with the counting-sort columns on the library's fixed scratch."""
+    if mem == CHAP_MEM_HOST and want_vars and xhat is None:
+        xhat = np.zeros(n)
+        score_half = np.zeros(n, np.int64)
+        dnviol = np.zeros(n, np.int32)
+    mv = chap_move()
+    _check(h, load().chap_bs_best_shift_static_scratch(h, _ptr(xhat), _ptr(score_half), _ptr(dnviol),
+                                                       C.byref(mv), mem))
     return xhat, score_half, dnviol, mv
 
 

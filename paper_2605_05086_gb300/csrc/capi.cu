@@ -41,6 +41,7 @@ struct chap_bs {
     int g_iters = 0;
     bool broken = false;
     bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
+    int64_t hist_bins = 0;     // counting-sort bins of the instance
     std::string err;
 };
 
@@ -501,6 +502,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     Tile *th_d = dalloc<Tile>(h, tiles_hist.size());
     HistCol *hc_d = dalloc<HistCol>(h, hcols.size());
     d.hbins = dalloc<HBin>(h, hist_bins);
+    h->hist_bins = hist_bins;
     d.hacc = dalloc<HistAcc>(h, hcols.size());
     h->t_xhat = dalloc<double>(h, n);
     h->t_s = dalloc<long long>(h, n);
@@ -741,6 +743,46 @@ chap_status chap_bs_best_shift(chap_bs *h, double *xhat, int64_t *score_half, in
     CK(h, launch_eval_gated(h->dev, h->plan, o, 0, h->st), "best-shift kernels");
     CK(h, launch_select_gated(h->dev, h->plan, 0, h->st), "selection kernel");
     if (h->plan.profile) h->prof_valid = true;
+    if (host && h->n) {
+        if (xhat) CK(h, cudaMemcpyAsync(xhat, h->t_xhat, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st), "copy xhat");
+        if (score_half) CK(h, cudaMemcpyAsync(score_half, h->t_s, sizeof(long long) * h->n, cudaMemcpyDeviceToHost, h->st), "copy scores");
+        if (dnviol) CK(h, cudaMemcpyAsync(dnviol, h->t_dc, sizeof(int) * h->n, cudaMemcpyDeviceToHost, h->st), "copy dnviol");
+    }
+    if (best || host) {
+        chap_status s = read_ctl(h);
+        if (s != CHAP_OK) return s;
+        if (best) {
+            const Ctl &c = *h->h_ctl;
+            best->var = c.mv_var;
+            best->dnviol = c.mv_dc;
+            best->score_half = c.mv_s;
+            best->old_value = c.mv_old;
+            best->new_value = c.mv_new;
+        }
+    }
+    return CHAP_OK;
+}
+
+chap_status chap_bs_best_shift_static_scratch(chap_bs *h, double *xhat, int64_t *score_half, int32_t *dnviol,
+                                              chap_move *best, int32_t mem)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    if (h->hist_bins > kStaticHistBins || h->info.n_hist_cols > kStaticHistCols)
+        return fail(h, CHAP_E_UNSUPPORTED,
+                    "counting-sort columns need " + std::to_string(h->hist_bins) + " bins and " +
+                        std::to_string(h->info.n_hist_cols) + " accumulators; the static scratch holds " +
+                        std::to_string(kStaticHistBins) + " and " + std::to_string(kStaticHistCols));
+    Dev d = h->dev;
+    CK(h, static_hist_scratch(&d.hbins, &d.hacc), "static scratch address");
+    VarOut o{nullptr, nullptr, nullptr};
+    bool host = mem == CHAP_MEM_HOST;
+    if (xhat) o.xhat = host ? h->t_xhat : xhat;
+    if (score_half) o.s = host ? h->t_s : reinterpret_cast<long long *>(score_half);
+    if (dnviol) o.dc = host ? h->t_dc : dnviol;
+    CK(h, launch_eval_gated(d, h->plan, o, 0, h->st), "best-shift kernels");
+    CK(h, launch_select_gated(d, h->plan, 0, h->st), "selection kernel");
     if (host && h->n) {
         if (xhat) CK(h, cudaMemcpyAsync(xhat, h->t_xhat, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st), "copy xhat");
         if (score_half) CK(h, cudaMemcpyAsync(score_half, h->t_s, sizeof(long long) * h->n, cudaMemcpyDeviceToHost, h->st), "copy scores");

@@ -198,6 +198,9 @@ struct LaunchPlan {
 // Kernel launchers (kernels.cu).  All are asynchronous on `st`; `gate` makes a
 // kernel return at once when the run's done flag is set (graph replays).
 cudaError_t setup_kernel_attributes(const LaunchPlan &p);
+// Device addresses of the fixed counting-sort scratch (kStaticHistBins bins,
+// kStaticHistCols accumulators) on the current device.
+cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc);
 int bin_grid_size(int ncols);  // persistent grids of the binary and short-column kernels on the current device
 int nb_grid_size(int ncols);
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
@@ -218,6 +221,8 @@ constexpr int kCtaThreads = 512;
 constexpr int kHistMaxDomain = 4096;    // largest integer domain of the multi-CTA counting sort
 constexpr int kHistChunk = 16384;       // matrix entries per counting-sort CTA
 constexpr int kHistThreads = 512;
+constexpr int kStaticHistBins = 1 << 16;  // fixed counting-sort scratch: bins (24 B each, 1.5 MiB)
+constexpr int kStaticHistCols = 256;      // and columns
 constexpr int kApplyThreads = 256;
 constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
 

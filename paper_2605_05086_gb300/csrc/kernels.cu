@@ -1804,6 +1804,38 @@ int nb_grid_size(int ncols)
     return (int)(need < cap ? need : cap);
 }
 
+// Fixed-size scratch of the counting-sort columns for callers that do not
+// use the per-handle allocation (chap_bs_best_shift_static_scratch).  Zero at
+// module load; k_eval_hist returns every bin and accumulator it touched to
+// zero before it finishes, so consecutive passes find it cleared.  Shared by
+// every handle of the process: overlapping passes through it race.
+static __device__ __align__(256) HBin g_static_bins[kStaticHistBins];
+static __device__ __align__(256) HistAcc g_static_acc[kStaticHistCols];
+
+cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc)
+{
+    // resolved once per device, with that device current
+    constexpr int kMaxDevices = 64;
+    static HBin *s_bins[kMaxDevices] = {};
+    static HistAcc *s_acc[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!s_bins[dev] || !s_acc[dev]) {
+        void *pb = nullptr, *pa = nullptr;
+        e = cudaGetSymbolAddress(&pb, g_static_bins);
+        if (e != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(&pa, g_static_acc);
+        if (e != cudaSuccess) return e;
+        s_bins[dev] = static_cast<HBin *>(pb);
+        s_acc[dev] = static_cast<HistAcc *>(pa);
+    }
+    *bins = s_bins[dev];
+    *acc = s_acc[dev];
+    return cudaSuccess;
+}
+
 cudaError_t setup_kernel_attributes(const LaunchPlan &p)
 {
     cudaError_t e = cudaSuccess;
