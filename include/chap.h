@@ -139,7 +139,8 @@ typedef struct chap_info {
     int32_t grid_nb;          /* CTAs of the persistent short-column kernel (0: none) */
     int64_t bytes_bin;        /* algorithmic bytes of one launch of the binary-flip kernel */
     int64_t bytes_nb;         /* algorithmic bytes of one launch of the short-column kernel */
-    int32_t reserved[2];
+    int64_t bytes_cta;        /* ... of the CTA-sort kernel (long non-integer columns) */
+    int64_t bytes_hist;       /* ... of the counting-sort kernel (long integer columns) */
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);

@@ -64,7 +64,8 @@ class chap_info(C.Structure):
                 ("nnz", C.c_int64), ("nnz_int_rows", C.c_int64), ("nnz_fp_rows", C.c_int64),
                 ("bytes_per_pass", C.c_int64), ("eval_blocks", C.c_int32), ("n_hist_cols", C.c_int32),
                 ("launches_per_step", C.c_int32), ("grid_bin", C.c_int32), ("grid_nb", C.c_int32),
-                ("bytes_bin", C.c_int64), ("bytes_nb", C.c_int64), ("reserved", C.c_int32 * 2)]
+                ("bytes_bin", C.c_int64), ("bytes_nb", C.c_int64), ("bytes_cta", C.c_int64),
+                ("bytes_hist", C.c_int64)]
 
 
 _lib = None

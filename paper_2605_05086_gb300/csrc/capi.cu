@@ -600,6 +600,10 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         in.grid_nb = n_tn;
         in.bytes_bin = bin_cols ? kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16) : 0;
         in.bytes_nb = nb_cols ? kernel_bytes(kind_base[T_NB], kind_base[T_NB + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;
+        const int ncta = kind_base[T_NB_CTA + 1] - kind_base[T_NB_CTA];
+        const int nhist = kind_base[T_NB_HIST + 1] - kind_base[T_NB_HIST];
+        in.bytes_cta = ncta ? kernel_bytes(kind_base[T_NB_CTA], kind_base[T_NB_CTA + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;
+        in.bytes_hist = nhist ? kernel_bytes(kind_base[T_NB_HIST], kind_base[T_NB_HIST + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;
     }
 
     std::vector<double> x0(n);
