@@ -266,6 +266,47 @@ CHAP_API chap_status chap_bs_step(struct chap_bs *h, chap_move *out);
  */
 CHAP_API chap_status chap_tabu_run(struct chap_bs *h, const chap_options *opts, chap_tabu_result *result);
 
+/*
+ * Batched tabu chains (growth path; Sec. 3.1, "Parallel Tabu Search Instances").
+ * Many independent chains over several instances advance together: one
+ * evaluation launch covers every (chain, 32-column tile), then one apply CTA
+ * per chain and one weight-bump launch; K iterations are captured into one
+ * CUDA graph and replayed.  Each chain follows exactly the single-handle
+ * iteration (chap_bs_step) of its instance with its own tenure, from
+ * x0 = 0, unit weights, no tabu.  Supported instances: every variable binary,
+ * every row integral (integer coefficients and rhs), fewer than 2^22 variables.
+ *
+ * chap_batch_create: probs[n_probs] (host arrays, as chap_bs_create);
+ *   chain_prob[n_chains] the instance of each chain, chain_tenure[n_chains] its
+ *   tenure.  CHAP_E_UNSUPPORTED for an instance outside the supported class.
+ * chap_batch_run: advances every chain by up to max_iters iterations (stops a
+ *   chain at its first nviol = 0 when stop_at_feasible), graph_iters iterations
+ *   per graph replay; res[n_chains] (host, optional) receives per-chain
+ *   counters (chap_chain_result), *seconds (optional) the wall time.
+ * chap_batch_autotune: times every schedule (lanes per column 4 / 8 / 16 x
+ *   CTAs per SM 2 / 4 / 8) for `iters` iterations from the initial state, keeps
+ *   the fastest (chosen[2] host, optional) and restores the initial state.
+ * chap_batch_set_schedule: sets the schedule explicitly.
+ * chap_batch_reset: every chain back to its initial state.
+ * chap_batch_get_x: x of one chain (host double[n of its instance]).
+ */
+typedef struct chap_chain_result {
+    int64_t iters, moves, feasible_iter, final_nviol, best_nviol;
+    double time_to_feasible_s;  /* device time from the run's start, else -1 */
+} chap_chain_result;
+
+CHAP_API chap_status chap_batch_create(const chap_problem *probs, int32_t n_probs, const int32_t *chain_prob,
+                                       const int32_t *chain_tenure, int32_t n_chains, void *stream,
+                                       struct chap_batch **out);
+CHAP_API chap_status chap_batch_destroy(struct chap_batch *b);
+CHAP_API chap_status chap_batch_run(struct chap_batch *b, int64_t max_iters, int32_t stop_at_feasible,
+                                    int32_t graph_iters, chap_chain_result *res, double *seconds);
+CHAP_API chap_status chap_batch_autotune(struct chap_batch *b, int32_t iters, int32_t *chosen);
+CHAP_API chap_status chap_batch_set_schedule(struct chap_batch *b, int32_t lanes_per_column, int32_t ctas_per_sm);
+CHAP_API chap_status chap_batch_reset(struct chap_batch *b);
+CHAP_API chap_status chap_batch_get_x(struct chap_batch *b, int32_t chain, double *x);
+CHAP_API const char *chap_batch_last_error(const struct chap_batch *b);
+
 CHAP_API const char *chap_status_str(chap_status s);
 CHAP_API const char *chap_last_error(const struct chap_bs *h);
 

@@ -25,6 +25,8 @@ EXPORTED = [
     "chap_bs_set_checkpoint", "chap_bs_get_state", "chap_bs_residuals", "chap_bs_best_shift",
     "chap_bs_apply", "chap_bs_step", "chap_tabu_run", "chap_status_str", "chap_last_error",
     "chap_bs_profile", "chap_bs_kernel_ms", "chap_bs_best_shift_static_scratch",
+    "chap_batch_create", "chap_batch_destroy", "chap_batch_run", "chap_batch_autotune", "chap_batch_set_schedule",
+    "chap_batch_reset", "chap_batch_get_x", "chap_batch_last_error",
 ]
 
 
@@ -104,6 +106,14 @@ def load(build_if_missing: bool = True):
         "chap_bs_profile": (I32, [P, I32]),
         "chap_bs_kernel_ms": (I32, [P, P]),
         "chap_bs_best_shift_static_scratch": (I32, [P, P, P, P, P, I32]),
+        "chap_batch_create": (I32, [P, I32, P, P, I32, P, P]),
+        "chap_batch_destroy": (I32, [P]),
+        "chap_batch_run": (I32, [P, I64, I32, I32, P, P]),
+        "chap_batch_autotune": (I32, [P, I32, P]),
+        "chap_batch_set_schedule": (I32, [P, I32, I32]),
+        "chap_batch_reset": (I32, [P]),
+        "chap_batch_get_x": (I32, [P, I32, P]),
+        "chap_batch_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -306,3 +316,73 @@ class BestShift:
         for k, v in kw.items():
             setattr(o, k, v)
         return chap_tabu_run(self.h, o)
+
+
+class chap_chain_result(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("moves", C.c_int64), ("feasible_iter", C.c_int64),
+                ("final_nviol", C.c_int64), ("best_nviol", C.c_int64), ("time_to_feasible_s", C.c_double)]
+
+
+class BatchChains:
+    """Independent tabu chains over several all-binary integral instances (chap_batch_*)."""
+
+    def __init__(self, probs, chain_prob, chain_tenure, stream=None):
+        lib = load()
+        self._keep = []
+        arr = (chap_problem * len(probs))()
+        for k, prob in enumerate(probs):
+            keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
+                (prob.row_ptr, np.int64), (prob.col_idx, np.int32), (prob.row_val, np.float64),
+                (prob.col_ptr, np.int64), (prob.row_idx, np.int32), (prob.col_val, np.float64),
+                (prob.lb, np.float64), (prob.ub, np.float64), (prob.obj, np.float64), (prob.rhs, np.float64),
+                (prob.vtype, np.uint8), (prob.sense, np.uint8))]
+            self._keep.append(keep)
+            arr[k] = chap_problem(prob.n, prob.m, int(prob.row_ptr[-1]), *[_ptr(a) for a in keep])
+        self.chain_prob = np.ascontiguousarray(chain_prob, np.int32)
+        self.chain_tenure = np.ascontiguousarray(chain_tenure, np.int32)
+        self.n_chains = len(self.chain_prob)
+        self.n_of = [p.n for p in probs]
+        self.h = C.c_void_p()
+        st = lib.chap_batch_create(arr, len(probs), _ptr(self.chain_prob), _ptr(self.chain_tenure), self.n_chains,
+                                   _stream(stream), C.byref(self.h))
+        if st != CHAP_OK:
+            raise ChapError(st, "chap_batch_create: " + lib.chap_status_str(st).decode())
+
+    def _check(self, st):
+        if st != CHAP_OK:
+            lib = load()
+            raise ChapError(st, lib.chap_batch_last_error(self.h).decode() or lib.chap_status_str(st).decode())
+
+    def run(self, max_iters, stop_at_feasible=True, graph_iters=64):
+        res = (chap_chain_result * self.n_chains)()
+        secs = C.c_double()
+        self._check(load().chap_batch_run(self.h, int(max_iters), 1 if stop_at_feasible else 0, int(graph_iters),
+                                          res, C.byref(secs)))
+        return list(res), secs.value
+
+    def autotune(self, iters=5):
+        ch = np.zeros(2, np.int32)
+        self._check(load().chap_batch_autotune(self.h, int(iters), _ptr(ch)))
+        return int(ch[0]), int(ch[1])
+
+    def set_schedule(self, lanes_per_column, ctas_per_sm):
+        self._check(load().chap_batch_set_schedule(self.h, int(lanes_per_column), int(ctas_per_sm)))
+
+    def reset(self):
+        self._check(load().chap_batch_reset(self.h))
+
+    def x(self, chain):
+        out = np.zeros(self.n_of[self.chain_prob[chain]])
+        self._check(load().chap_batch_get_x(self.h, int(chain), _ptr(out)))
+        return out
+
+    def close(self):
+        if self.h:
+            load().chap_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

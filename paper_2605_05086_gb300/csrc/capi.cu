@@ -224,6 +224,11 @@ chap_status load_state(chap_bs *h, const double *x, const int *w, const int *tab
 
 }  // namespace
 
+namespace chap {
+// Validation of a problem, shared with the batched path.
+chap_status validate_problem(const chap_problem *p, std::string &msg) { return validate(p, msg); }
+}  // namespace chap
+
 extern "C" {
 
 void chap_options_default(chap_options *o)
