@@ -4,6 +4,7 @@
 // of the tabu loop (Sec. 3.1, "Kernel Specialization", last point).
 #include "../../include/chap.h"
 #include "chap_internal.h"
+#include "chap_handle.h"
 
 #include <algorithm>
 #include <chrono>
@@ -17,33 +18,6 @@
 
 using namespace chap;
 
-struct chap_bs {
-    cudaStream_t st = nullptr;
-    cudaStream_t cap_st = nullptr;
-    chap_options opt{};
-    chap_info info{};
-    int n = 0, m = 0, m_norm = 0;
-    std::vector<double> lb, ub, obj;
-    std::vector<uint8_t> vtype, row_eq;
-    std::vector<int> nrow_base;
-    std::vector<void *> allocs;
-    Dev dev{};
-    LaunchPlan plan{};
-    // device scratch for host-memory outputs
-    double *t_xhat = nullptr;
-    long long *t_s = nullptr;
-    int *t_dc = nullptr;
-    int *t_w = nullptr;
-    double *t_r = nullptr;
-    long long *t_tabu = nullptr;
-    Ctl *h_ctl = nullptr;  // pinned
-    cudaGraphExec_t gexec = nullptr;
-    int g_iters = 0;
-    bool broken = false;
-    bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
-    int64_t hist_bins = 0;     // counting-sort bins of the instance
-    std::string err;
-};
 
 namespace {
 
@@ -227,6 +201,15 @@ chap_status load_state(chap_bs *h, const double *x, const int *w, const int *tab
 namespace chap {
 // Validation of a problem, shared with the batched path.
 chap_status validate_problem(const chap_problem *p, std::string &msg) { return validate(p, msg); }
+
+cudaError_t bs_pass(chap_bs *h, const VarOut &o)
+{
+    cudaError_t e = launch_eval_gated(h->dev, h->plan, o, 0, h->st);
+    if (e == cudaSuccess) e = launch_select_gated(h->dev, h->plan, 0, h->st);
+    return e;
+}
+
+cudaError_t bs_apply_selected(chap_bs *h) { return launch_apply_gated(h->dev, h->plan, 0, h->st); }
 }  // namespace chap
 
 extern "C" {

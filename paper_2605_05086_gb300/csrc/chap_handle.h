@@ -1,0 +1,46 @@
+// The handle behind struct chap_bs (shared by the C ABI files).
+#pragma once
+#include "../../include/chap.h"
+#include "chap_internal.h"
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+struct chap_bs {
+    using Dev = chap::Dev;
+    using LaunchPlan = chap::LaunchPlan;
+    using Ctl = chap::Ctl;
+    cudaStream_t st = nullptr;
+    cudaStream_t cap_st = nullptr;
+    chap_options opt{};
+    chap_info info{};
+    int n = 0, m = 0, m_norm = 0;
+    std::vector<double> lb, ub, obj;
+    std::vector<uint8_t> vtype, row_eq;
+    std::vector<int> nrow_base;
+    std::vector<void *> allocs;
+    Dev dev{};
+    LaunchPlan plan{};
+    // device scratch for host-memory outputs
+    double *t_xhat = nullptr;
+    long long *t_s = nullptr;
+    int *t_dc = nullptr;
+    int *t_w = nullptr;
+    double *t_r = nullptr;
+    long long *t_tabu = nullptr;
+    Ctl *h_ctl = nullptr;  // pinned
+    cudaGraphExec_t gexec = nullptr;
+    int g_iters = 0;
+    bool broken = false;
+    bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
+    int64_t hist_bins = 0;     // counting-sort bins of the instance
+    std::string err;
+};
+
+namespace chap {
+// A best-shift pass (evaluation kernels + selection) on the handle's stream,
+// with optional device per-variable outputs; the apply of the selected move.
+cudaError_t bs_pass(chap_bs *h, const VarOut &o);
+cudaError_t bs_apply_selected(chap_bs *h);
+}  // namespace chap
