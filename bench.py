@@ -220,6 +220,68 @@ def run_batch(args):
     return 0
 
 
+def run_learned(args):
+    """Learned proposal on the set-cover 200k-var instance: 5M (feature, exact
+    score) pairs logged by the exact driver on a training instance of the same
+    family (another seed), network trained on the GPU, then the learned loop
+    (top-k 4096, exact pass every 50 iterations) against the plain exact driver
+    on the evaluation instance, both from x0 until feasible or the cap."""
+    import torch
+    from paper_2605_05086_gb300 import chap, learn
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream().cuda_stream
+    cap = args.learned_cap
+    train_prob = inst.gen_setcover(seed=21, n=200_000, m=100_000, k=8)
+    prob = inst.make("setcover_200k")
+    t0 = time.perf_counter()
+    tb = chap.BestShift(train_prob, stream=stream, tenure=10)
+    x, t = learn.log_pairs(tb, passes=25, iters_between=40)
+    tb.close()
+    t_log = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    wbf, _, curve = learn.train(x, t, epochs=2, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    plain = chap.BestShift(prob, stream=stream, tenure=10)
+    rp = plain.run(max_iters=cap, stop_at_feasible=1, graph_iters=64)
+    plain.close()
+    clocks = Clocks(torch.cuda.current_device())
+    lh = chap.BestShift(prob, stream=stream, tenure=10)
+    clocks.start()
+    rl = chap.chap_learned_run(lh.h, wbf, topk=4096, exact_every=50, propose_every=args.propose_every,
+                               max_iters=cap, stop_at_feasible=True)
+    clk = clocks.stop()
+    lh.close()
+    value = rl.moves / rl.seconds
+    line = {
+        "metric": "tabu moves/s, learned proposal (top-k 4096, exact pass every 50), set-cover 200k vars",
+        "value": value, "unit": "moves/s", "n_gpus": 1, "steps": int(rl.iters), "warmup": 0,
+        "ms_per_step": rl.seconds * 1e3 / max(1, rl.iters), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 network / int64 exact scores", "data": "synthetic",
+        "config": {"workload": "learned_200k", "n": prob.n, "m": prob.m, "nnz": prob.nnz, "topk": 4096,
+                   "exact_every": 50, "propose_every": args.propose_every, "iteration_cap": cap,
+                   "training": {"pairs": int(x.shape[0]), "log_seconds": t_log, "train_seconds": t_train,
+                                "epochs": 2, "batch": 8192, "loss_per_epoch": curve,
+                                "instance": "set cover 200k vars, seed 21"},
+                   "learned": {"iters": rl.iters, "moves": rl.moves, "seconds": rl.seconds,
+                               "feasible_iter": rl.feasible_iter, "time_to_feasible_s": rl.time_to_feasible_s,
+                               "exact_passes": rl.exact_passes, "top1_misses": rl.misses,
+                               "top1_miss_rate": rl.misses / max(1, rl.exact_passes),
+                               "final_nviol": rl.final_nviol},
+                   "plain_exact": {"iters": rp.iters, "moves": rp.moves, "seconds": rp.seconds,
+                                   "moves_per_s": rp.moves / rp.seconds, "feasible_iter": rp.feasible_iter,
+                                   "time_to_feasible_s": rp.time_to_feasible_s, "final_nviol": rp.final_nviol}},
+        "e2e": {"value": rl.moves / (rl.seconds + t_log + t_train), "unit": "moves/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "call": "pair logging + training + chap_learned_run (instance already on the device)"},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def profiled_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` from the committed ncu summary of this
     workload, when that summary was taken on the current kernel source (its
@@ -248,13 +310,21 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="general_200k", choices=sorted(inst.WORKLOADS) + ["batch_64x4"])
+    ap.add_argument("--workload", default="general_200k", choices=sorted(inst.WORKLOADS) + ["batch_64x4", "learned_200k"])
     ap.add_argument("--batch-cap", type=int, default=20000, help="iteration cap per chain (batch_64x4)")
+    ap.add_argument("--learned-cap", type=int, default=300000, help="iteration cap (learned_200k)")
+    ap.add_argument("--propose-every", type=int, default=25, help="iterations between proposals (learned_200k)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph-iters", type=int, default=2000)
     args = ap.parse_args()
+    if args.workload == "learned_200k":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the learned path is compared against the GPU "
+                              "plain exact driver on the same instance instead"}))
+            return 0
+        return run_learned(args)
     if args.workload == "batch_64x4":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle runs one chain at a time; "

@@ -307,6 +307,59 @@ CHAP_API chap_status chap_batch_reset(struct chap_batch *b);
 CHAP_API chap_status chap_batch_get_x(struct chap_batch *b, int32_t chain, double *x);
 CHAP_API const char *chap_batch_last_error(const struct chap_batch *b);
 
+/*
+ * Learned move proposal (growth path; no counterpart in the paper).  A network
+ * 12 -> 64 -> 64 -> 1 with ReLU predicts every variable's best-shift score from
+ * 12 features; the exact best-shift evaluation then runs on the k variables
+ * with the largest predictions (ties: lower index) and a full exact pass every
+ * exact_every iterations supplies that iteration's move and judges the
+ * proposal (a miss: the exact best score exceeds the best score in the
+ * proposed subset).  Moves are always chosen by exact scores.
+ *
+ * Parameters: CHAP_MLP_PARAMS values in the order W1 [12 x 64] (row-major,
+ * input x output), b1 [64], W2 [64 x 64], b2 [64], w3 [64], b3; BF16 (uint16
+ * bits) for inference, FP32 masters for training.  Features per variable (BF16,
+ * row-major [n x 12]): x/(u-l), (x-l)/(u-l), (u-x)/(u-l), min(tabu age,64)/64,
+ * share of the column's halves that are violated, their share of sum w|a|,
+ * last exact score / (1 + max |score|), iterations since the exact pass / 50,
+ * log2(1 + column length)/16, is_binary, is_integer, c_j / max|c|.
+ *
+ * chap_bs_refresh_features: exact pass at the current state (scores and the
+ *   column features recorded for the proposal; no move).
+ * chap_bs_features: features of the current state into feat (device, may be
+ *   NULL) and the last exact scores scaled by 1/(1 + max|score|) into target
+ *   (device float[n], may be NULL): one training pair per variable.
+ * chap_bs_propose: features, predictions (pred: device float[n], may be NULL)
+ *   and the k selected variables (list: device int32[k], may be NULL).
+ * chap_learned_run: the learned tabu loop from the current state (all-binary
+ *   instances); propose_every: iterations between two proposals.
+ * chap_mlp_forward: y[n] = network(x[n x 12]) (device pointers).
+ * chap_mlp_loss_grad: adds the gradient of mean((y - t)^2) over the n rows to
+ *   grad[CHAP_MLP_PARAMS] and the sum of squared errors to loss[0] (device).
+ * chap_mlp_adam: one Adam step (beta 0.9 / 0.999, eps 1e-8) of the FP32
+ *   masters w32 with moments m, v from grad (cleared), writing the BF16 copy.
+ */
+#define CHAP_MLP_PARAMS 5057
+typedef struct chap_learned_options {
+    int32_t topk, exact_every, propose_every, stop_at_feasible;
+    int64_t max_iters;
+} chap_learned_options;
+typedef struct chap_learned_result {
+    int64_t iters, moves, feasible_iter, final_nviol, best_nviol, exact_passes, misses;
+    double seconds, time_to_feasible_s;
+} chap_learned_result;
+
+CHAP_API chap_status chap_bs_refresh_features(struct chap_bs *h);
+CHAP_API chap_status chap_bs_features(struct chap_bs *h, uint16_t *feat, float *target);
+CHAP_API chap_status chap_bs_propose(struct chap_bs *h, const uint16_t *weights, int32_t k, int32_t *list, float *pred);
+CHAP_API chap_status chap_learned_run(struct chap_bs *h, const uint16_t *weights, const chap_learned_options *lo,
+                                      chap_learned_result *res);
+CHAP_API chap_status chap_mlp_forward(const uint16_t *weights, const uint16_t *x, int64_t n, float *y, void *stream);
+CHAP_API chap_status chap_mlp_loss_grad(const uint16_t *weights, const uint16_t *x, const float *target, int64_t n,
+                                        float *grad, float *loss, void *stream);
+CHAP_API chap_status chap_mlp_adam(float *w32, uint16_t *wbf, float *m, float *v, float *grad, int32_t step, float lr,
+                                   void *stream);
+
 CHAP_API const char *chap_status_str(chap_status s);
 CHAP_API const char *chap_last_error(const struct chap_bs *h);
 

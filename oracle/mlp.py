@@ -113,3 +113,27 @@ def topk(scores, k):
     """Indices of the k largest scores, ties broken by the lower index."""
     order = np.lexsort((np.arange(len(scores)), -np.asarray(scores, np.float64)))
     return np.sort(order[:k])
+
+
+def column_stats(prob, x, w, feas_tol=0.0):
+    """Pass-time column features of every variable at assignment x with the
+    normalised rows' weights w (canonical order): the share of the column's
+    normalised halves that are violated, and their share of sum w |a|."""
+    from oracle import definition as D
+    rows = D.normalised_rows(prob, feas_tol)
+    halves = np.zeros(prob.n)
+    viol = np.zeros(prob.n)
+    wall = np.zeros(prob.n)
+    wviol = np.zeros(prob.n)
+    xs = [D.F(float(v)) for v in x]
+    for k, (coeffs, b, eps) in enumerate(rows):
+        v = D.activity(coeffs, xs) - b > eps
+        for j, a in coeffs.items():
+            halves[j] += 1
+            wall[j] += w[k] * abs(float(a))
+            if v:
+                viol[j] += 1
+                wviol[j] += w[k] * abs(float(a))
+    colviol = np.where(halves > 0, viol / np.maximum(halves, 1), 0.0)
+    colwv = np.where(wall > 0, wviol / np.where(wall > 0, wall, 1.0), 0.0)
+    return colviol, colwv

@@ -27,6 +27,8 @@ EXPORTED = [
     "chap_bs_profile", "chap_bs_kernel_ms", "chap_bs_best_shift_static_scratch",
     "chap_batch_create", "chap_batch_destroy", "chap_batch_run", "chap_batch_autotune", "chap_batch_set_schedule",
     "chap_batch_reset", "chap_batch_get_x", "chap_batch_last_error",
+    "chap_bs_refresh_features", "chap_bs_features", "chap_bs_propose", "chap_learned_run", "chap_mlp_forward",
+    "chap_mlp_loss_grad", "chap_mlp_adam",
 ]
 
 
@@ -114,6 +116,13 @@ def load(build_if_missing: bool = True):
         "chap_batch_reset": (I32, [P]),
         "chap_batch_get_x": (I32, [P, I32, P]),
         "chap_batch_last_error": (C.c_char_p, [P]),
+        "chap_bs_refresh_features": (I32, [P]),
+        "chap_bs_features": (I32, [P, P, P]),
+        "chap_bs_propose": (I32, [P, P, I32, P, P]),
+        "chap_learned_run": (I32, [P, P, P, P]),
+        "chap_mlp_forward": (I32, [P, P, I64, P, P]),
+        "chap_mlp_loss_grad": (I32, [P, P, P, I64, P, P, P]),
+        "chap_mlp_adam": (I32, [P, P, P, P, P, I32, C.c_float, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -386,3 +395,67 @@ class BatchChains:
             self.close()
         except Exception:
             pass
+
+
+MLP_PARAMS = 5057
+
+
+class chap_learned_options(C.Structure):
+    _fields_ = [("topk", C.c_int32), ("exact_every", C.c_int32), ("propose_every", C.c_int32),
+                ("stop_at_feasible", C.c_int32), ("max_iters", C.c_int64)]
+
+
+class chap_learned_result(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("moves", C.c_int64), ("feasible_iter", C.c_int64),
+                ("final_nviol", C.c_int64), ("best_nviol", C.c_int64), ("exact_passes", C.c_int64),
+                ("misses", C.c_int64), ("seconds", C.c_double), ("time_to_feasible_s", C.c_double)]
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (None passes NULL)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def chap_bs_refresh_features(h):
+    _check(h, load().chap_bs_refresh_features(h))
+
+
+def chap_bs_features(h, feat=None, target=None):
+    """feat: torch int16 [n, 12] (BF16 bits), target: torch float32 [n] (device)."""
+    _check(h, load().chap_bs_features(h, _dptr(feat), _dptr(target)))
+
+
+def chap_bs_propose(h, weights, k, lst=None, pred=None):
+    _check(h, load().chap_bs_propose(h, _dptr(weights), int(k), _dptr(lst), _dptr(pred)))
+
+
+def chap_learned_run(h, weights, topk=4096, exact_every=50, propose_every=1, max_iters=1000, stop_at_feasible=True):
+    lo = chap_learned_options(int(topk), int(exact_every), int(propose_every), 1 if stop_at_feasible else 0,
+                              int(max_iters))
+    res = chap_learned_result()
+    _check(h, load().chap_learned_run(h, _dptr(weights), C.byref(lo), C.byref(res)))
+    return res
+
+
+def _stream_of(stream):
+    return _stream(stream)
+
+
+def chap_mlp_forward(weights, x, y, stream=None):
+    st = load().chap_mlp_forward(_dptr(weights), _dptr(x), int(x.shape[0]), _dptr(y), _stream(stream))
+    if st != CHAP_OK:
+        raise ChapError(st, "chap_mlp_forward")
+
+
+def chap_mlp_loss_grad(weights, x, target, grad, loss, stream=None):
+    st = load().chap_mlp_loss_grad(_dptr(weights), _dptr(x), _dptr(target), int(x.shape[0]), _dptr(grad),
+                                   _dptr(loss), _stream(stream))
+    if st != CHAP_OK:
+        raise ChapError(st, "chap_mlp_loss_grad")
+
+
+def chap_mlp_adam(w32, wbf, m, v, grad, step, lr, stream=None):
+    st = load().chap_mlp_adam(_dptr(w32), _dptr(wbf), _dptr(m), _dptr(v), _dptr(grad), int(step), float(lr),
+                              _stream(stream))
+    if st != CHAP_OK:
+        raise ChapError(st, "chap_mlp_adam")

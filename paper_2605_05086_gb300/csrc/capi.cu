@@ -130,6 +130,7 @@ chap_status validate(const chap_problem *p, std::string &msg)
 
 void free_all(chap_bs *h)
 {
+    learn_free(h);
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();

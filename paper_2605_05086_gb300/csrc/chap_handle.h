@@ -35,6 +35,7 @@ struct chap_bs {
     bool broken = false;
     bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
     int64_t hist_bins = 0;     // counting-sort bins of the instance
+    void *learn = nullptr;     // state of the learned driver (learned.cu), created on first use
     std::string err;
 };
 
@@ -43,4 +44,5 @@ namespace chap {
 // with optional device per-variable outputs; the apply of the selected move.
 cudaError_t bs_pass(chap_bs *h, const VarOut &o);
 cudaError_t bs_apply_selected(chap_bs *h);
+void learn_free(chap_bs *h);   // releases h->learn (learned.cu)
 }  // namespace chap
