@@ -91,6 +91,18 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def reduce_over_ranks(seconds, moves, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the moves of all ranks (a collective over the initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mv = torch.tensor([float(moves)], dtype=torch.float64, device=device)
+    dist.all_reduce(mv)
+    return float(t.item()), int(round(mv.item()))
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -420,15 +432,9 @@ def main():
         e2e_moves += r.moves
     e2e_s = time.perf_counter() - t0
 
-    t_max = total_s
-    moves_all = moves
+    t_max, moves_all = total_s, moves
     if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        mv = torch.tensor([float(moves)], device="cuda")
-        dist.all_reduce(mv)
-        moves_all = int(mv.item())
+        t_max, moves_all = reduce_over_ranks(total_s, moves, "cuda")
     if rank == 0:
         peak, peak_kind = peaks()
         # dominant kernel of the pass: the longest of the evaluation kernels
