@@ -129,9 +129,15 @@ def cpu_oracle_rate(prob, target_s=12.0, seed=0):
         done += len(vs)
         size *= 2
     pass_s = t_total * prob.n / done
+    # the same on one thread, on a sample of a quarter of the time
+    vs1 = order[:max(64, done // 8)]
+    t0 = time.perf_counter()
+    orc.best_shift(st["x"], st["w"], st["tabu_inc"], st["tabu_dec"], 0, nv, nv, vars=vs1, nthreads=1)
+    pass1 = (time.perf_counter() - t0) * prob.n / len(vs1)
     return {"value": 1.0 / pass_s, "unit": "moves/s", "cores": max_threads(), "kind": "oracle",
             "sample": f"oracle best shift of {done} of {prob.n} variables at x0 "
-                      f"({t_total:.1f} s), extrapolated to one full pass per move"}
+                      f"({t_total:.1f} s), extrapolated to one full pass per move",
+            "one_thread": {"value": 1.0 / pass1, "sample_vars": int(len(vs1))}}
 
 
 def run_reference(args):
@@ -232,6 +238,42 @@ def run_batch(args):
     return 0
 
 
+def run_multiclimb(args):
+    """Many climbers on one instance sharing its matrix (32 chains, tenures 5..50,
+    set cover 200k vars) against one chain of the same path, equal iteration cap."""
+    import torch
+    from paper_2605_05086_gb300 import chap
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream().cuda_stream
+    prob = inst.make("setcover_200k")
+    cap = args.batch_cap
+    tenures = [int(t) for t in np.linspace(5, 50, 32)]
+    res = {}
+    for name, ten in (("single", [10]), ("multi", tenures)):
+        b = chap.BatchChains([prob], [0] * len(ten), ten, stream=stream)
+        sched = b.autotune(iters=3)
+        r, secs = b.run(max_iters=cap, stop_at_feasible=True, graph_iters=64)
+        res[name] = dict(chains=len(ten), seconds=secs, moves=sum(x.moves for x in r),
+                         moves_per_s=sum(x.moves for x in r) / secs, feasible=sum(x.feasible_iter >= 0 for x in r),
+                         first_feasible_s=min([x.time_to_feasible_s for x in r if x.feasible_iter >= 0] or [-1.0]),
+                         schedule=list(sched))
+        b.close()
+    value = res["multi"]["moves_per_s"]
+    print(json.dumps({
+        "metric": "summed tabu moves/s, 32 climbers sharing one set-cover 200k-var instance",
+        "value": value, "unit": "moves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": res["multi"]["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "multiclimb_200k", "n": prob.n, "m": prob.m, "nnz": prob.nnz,
+                   "iteration_cap_per_chain": cap, "tenures": tenures, "multi": res["multi"],
+                   "single_chain": res["single"],
+                   "speedup_vs_single_chain": value / res["single"]["moves_per_s"]},
+        "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": None, "clocks": None}))
+    return 0
+
+
 def run_learned(args):
     """Learned proposal on the set-cover 200k-var instance: 5M (feature, exact
     score) pairs logged by the exact driver on a training instance of the same
@@ -322,7 +364,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="general_200k", choices=sorted(inst.WORKLOADS) + ["batch_64x4", "learned_200k"])
+    ap.add_argument("--workload", default="general_200k", choices=sorted(inst.WORKLOADS) + ["batch_64x4", "learned_200k", "multiclimb_200k"])
     ap.add_argument("--batch-cap", type=int, default=20000, help="iteration cap per chain (batch_64x4)")
     ap.add_argument("--learned-cap", type=int, default=300000, help="iteration cap (learned_200k)")
     ap.add_argument("--propose-every", type=int, default=25, help="iterations between proposals (learned_200k)")
@@ -331,6 +373,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph-iters", type=int, default=2000)
     args = ap.parse_args()
+    if args.workload == "multiclimb_200k":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "compared against one chain of the same GPU path"}))
+            return 0
+        return run_multiclimb(args)
     if args.workload == "learned_200k":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the learned path is compared against the GPU "
