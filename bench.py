@@ -114,6 +114,7 @@ def cpu_oracle_rate(prob, target_s=12.0, seed=0):
     """The oracle's best shift on a seeded sample of variables at x0, extrapolated to
     one full pass; one pass = one tabu move, so moves/s = 1 / pass time."""
     from oracle.oracle import Oracle, max_threads
+    cores = max_threads()
     orc = Oracle(prob)
     st = orc.initial_state()
     _, _, nv = orc.residuals(st["x"])
@@ -134,7 +135,7 @@ def cpu_oracle_rate(prob, target_s=12.0, seed=0):
     t0 = time.perf_counter()
     orc.best_shift(st["x"], st["w"], st["tabu_inc"], st["tabu_dec"], 0, nv, nv, vars=vs1, nthreads=1)
     pass1 = (time.perf_counter() - t0) * prob.n / len(vs1)
-    return {"value": 1.0 / pass_s, "unit": "moves/s", "cores": max_threads(), "kind": "oracle",
+    return {"value": 1.0 / pass_s, "unit": "moves/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle best shift of {done} of {prob.n} variables at x0 "
                       f"({t_total:.1f} s), extrapolated to one full pass per move",
             "one_thread": {"value": 1.0 / pass1, "sample_vars": int(len(vs1))}}

@@ -349,8 +349,9 @@ void orc_best_shift(const orc_t *h, const double *x, const int32_t *w,
 {
     int32_t count = vars ? nv : h->n;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
+    /* the thread count applies to this call only */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
 #endif
     for (int32_t q = 0; q < count; ++q) {
         int32_t j = vars ? vars[q] : q;
