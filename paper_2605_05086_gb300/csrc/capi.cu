@@ -454,7 +454,15 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     const int nb_cols = kind_base[T_NB + 1] - kind_base[T_NB];
     const int n_tn = nb_cols > 0 ? nb_grid_size(nb_cols) : 0;
     const int bin_cols = kind_base[T_BIN + 1] - kind_base[T_BIN];
-    const int n_tb = bin_cols > 0 ? bin_grid_size(bin_cols) : 0, n_tc = (int)tiles_cta.size();
+    // lanes per binary column: enough for one or two rounds of a mean-length column
+    int bin_G = 8;
+    if (bin_cols > 0) {
+        const double mean = (double)((ci_ptr[kind_base[T_BIN + 1]] - ci_ptr[kind_base[T_BIN]]) +
+                                     (cf_ptr[kind_base[T_BIN + 1]] - cf_ptr[kind_base[T_BIN]])) / bin_cols;
+        bin_G = (mean <= kBinG2MaxLen && bin_cols >= kBinG2MinCols) ? 2
+                : mean <= kBinG4MaxLen ? 4 : (mean <= kBinG8MaxLen ? 8 : 16);
+    }
+    const int n_tb = bin_cols > 0 ? bin_grid_size(bin_cols, bin_G) : 0, n_tc = (int)tiles_cta.size();
     const int slot_hist = n_tb + n_tn + n_tc;
     for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = slot_hist + (int)q;
     const int n_bb = slot_hist + (int)hcols.size();
@@ -543,7 +551,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     if (e == cudaSuccess && !hcols.empty()) e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
     LaunchPlan &pl = h->plan;
-    pl.bin_cols = bin_cols; pl.n_bin = n_tb;
+    pl.bin_cols = bin_cols; pl.n_bin = n_tb; pl.bin_G = bin_G;
     pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn;
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
     pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);
@@ -586,6 +594,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
             return b + per_col * (q1 - q0);
         };
         in.grid_bin = n_tb;
+        in.bin_lanes = bin_G;
         in.grid_nb = n_tn;
         in.bytes_bin = bin_cols ? kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16) : 0;
         in.bytes_nb = nb_cols ? kernel_bytes(kind_base[T_NB], kind_base[T_NB + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;

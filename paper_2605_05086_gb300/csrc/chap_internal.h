@@ -176,6 +176,7 @@ struct VarOut {
 struct LaunchPlan {
     int bin_cols;              // binary columns: positions [0, bin_cols)
     int n_bin;                 // CTAs of the persistent binary kernel (0: no binary column)
+    int bin_G;                 // lanes per binary column (4, 8 or 16, from the mean column length)
     int nb_q0, nb_cols;        // positions of the short non-binary columns (<= kWarpSortMax entries)
     int nb_grid;               // CTAs of the persistent warp-per-column kernel (0: no such column)
     const Tile *tiles_cta;
@@ -201,7 +202,8 @@ cudaError_t setup_kernel_attributes(const LaunchPlan &p);
 // Device addresses of the fixed counting-sort scratch (kStaticHistBins bins,
 // kStaticHistCols accumulators) on the current device.
 cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc);
-int bin_grid_size(int ncols);  // persistent grids of the binary and short-column kernels on the current device
+int bin_grid_size(int ncols, int G);  // persistent grids of the binary (G lanes per column) and
+                                      // short-column kernels on the current device
 int nb_grid_size(int ncols);
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
 cudaError_t launch_select_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
@@ -225,5 +227,9 @@ constexpr int kStaticHistBins = 1 << 16;  // fixed counting-sort scratch: bins (
 constexpr int kStaticHistCols = 256;      // and columns
 constexpr int kApplyThreads = 256;
 constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
+constexpr double kBinG2MaxLen = 6.0;    // mean binary column length up to which 2 lanes score a column
+constexpr int kBinG2MinCols = 32768;    // (and only with this many binary columns: small instances are latency-bound)
+constexpr double kBinG4MaxLen = 16.0;   // ... up to which 4 lanes do
+constexpr double kBinG8MaxLen = 1.0e30; // ... up to which 8 lanes do (16 above)
 
 }  // namespace chap

@@ -356,11 +356,11 @@ __device__ __forceinline__ bool gated_done(const Dev &d, int gate)
 //
 // The only move of a binary variable is the flip (Sec. 3.1, "Best Shift
 // Moves"); its score is the sum over the column of the penalty changes of the
-// normalised halves.  A group of kGrp lanes scores one column (four columns
-// per warp, persistent grid over the column quadruples, columns ordered by
-// length): the lanes read the column's nonzeros coalesced, gather the row
-// states and add the penalty changes branch-free in registers; a shuffle
-// reduction closes the column.
+// normalised halves.  A group of G lanes scores one column (32 / G columns
+// per warp, persistent grid, columns ordered by length; G = 2 .. 16 from the
+// mean column length): the lanes read the column's nonzeros coalesced, gather
+// the row states and add the penalty changes branch-free in registers; a
+// shuffle reduction closes the column.
 
 constexpr int kGrp = 8;                      // lanes per column
 constexpr int kGrpPerWarp = 32 / kGrp;       // columns per warp
@@ -375,13 +375,16 @@ __device__ __forceinline__ int flip_f(bool v0, bool v1, bool dec)
     return 2 * ((int)v0 - (int)v1) + ((v0 && v1) ? (dec ? 1 : -1) : 0);
 }
 
-// Largest value of v over the four groups of the warp.
-__device__ __forceinline__ int quad_max(int v)
+// Largest value of v over the groups of G lanes of the warp.
+template <int G>
+__device__ __forceinline__ int groups_max(int v)
 {
 #pragma unroll
-    for (int o2 = 16; o2 >= kGrp; o2 >>= 1) v = max(v, __shfl_xor_sync(FULLMASK, v, o2));
+    for (int o2 = 16; o2 >= G; o2 >>= 1) v = max(v, __shfl_xor_sync(FULLMASK, v, o2));
     return v;
 }
+
+__device__ __forceinline__ int quad_max(int v) { return groups_max<kGrp>(v); }
 
 // Flip score terms of one nonzero of an integral row (int64 residual r; a rise
 // of x_j changes r by a; the second half of an "=" row has residual -r and
@@ -425,7 +428,7 @@ __device__ __forceinline__ void flip_fp(const int4 &s0, const int4 &s1, double a
 // both halves), one nonzero per lane and round.  The row index and
 // coefficient of the next round are loaded while the current round's row
 // state is gathered, so a round waits for one memory latency, not two.
-template <bool FP, bool EQ>
+template <int G, bool FP, bool EQ>
 __device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, int sub, bool up, long long &s, int &dc)
 {
     using Val = typename std::conditional<FP, double, int>::type;
@@ -435,7 +438,7 @@ __device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, 
     int row = ok ? __ldg(rowp + sub) : 0;
     Val av = ok ? __ldg(valp + sub) : Val(0);
     const int4 z4 = make_int4(0, 0, 0, 0);
-    for (int base = 0; base < nmax; base += kGrp) {
+    for (int base = 0; base < nmax; base += G) {
         int4 s0, s1 = z4;
         if (!FP) {
             s0 = ok ? ld_row16(d.rs + row) : z4;
@@ -444,7 +447,7 @@ __device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, 
             s0 = ok ? __ldg(p) : z4;
             s1 = ok ? __ldg(p + 1) : z4;
         }
-        const int vn = base + kGrp + sub;
+        const int vn = base + G + sub;
         const bool okn = vn < n;
         const int rown = okn ? __ldg(rowp + vn) : 0;
         const Val avn = okn ? __ldg(valp + vn) : Val(0);
@@ -456,16 +459,18 @@ __device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, 
     }
 }
 
+template <int G>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, VarOut o, int gate)
 {
     if (gated_done(d, gate)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane / kGrp, sub = lane & (kGrp - 1);
+    constexpr int CPW = 32 / G;   // columns per warp
+    const int g = lane / G, sub = lane & (G - 1);
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
     Cand best{0, kNoVar, 0, 0.0};
-    const int nquad = (ncols + kGrpPerWarp - 1) / kGrpPerWarp;
+    const int nquad = (ncols + CPW - 1) / CPW;
     for (int qd = blockIdx.x * kEvalWarps + warp; qd < nquad; qd += gridDim.x * kEvalWarps) {
-        const int q = qd * kGrpPerWarp + g;
+        const int q = qd * CPW + g;
         const bool live = q < ncols;
         const int qq = live ? q : 0;
         const int ci0 = __ldg(d.ci_ptr + qq), cf0 = __ldg(d.cf_ptr + qq);
@@ -477,12 +482,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, Var
         const int nFs = live ? cfm - cf0 : 0, nFe = cf1 - (live ? cfm : cf1);
         long long s = 0;
         int dc = 0;
-        bin_part<false, false>(d, ci0, nIs, quad_max(nIs), sub, up, s, dc);
-        bin_part<false, true>(d, cim, nIe, quad_max(nIe), sub, up, s, dc);
-        bin_part<true, false>(d, cf0, nFs, quad_max(nFs), sub, up, s, dc);
-        bin_part<true, true>(d, cfm, nFe, quad_max(nFe), sub, up, s, dc);
+        bin_part<G, false, false>(d, ci0, nIs, groups_max<G>(nIs), sub, up, s, dc);
+        bin_part<G, false, true>(d, cim, nIe, groups_max<G>(nIe), sub, up, s, dc);
+        bin_part<G, true, false>(d, cf0, nFs, groups_max<G>(nFs), sub, up, s, dc);
+        bin_part<G, true, true>(d, cfm, nFe, groups_max<G>(nFe), sub, up, s, dc);
 #pragma unroll
-        for (int o2 = kGrp >> 1; o2 > 0; o2 >>= 1) {
+        for (int o2 = G >> 1; o2 > 0; o2 >>= 1) {
             s += __shfl_xor_sync(FULLMASK, s, o2);
             dc += __shfl_xor_sync(FULLMASK, dc, o2);
         }
@@ -1767,10 +1772,12 @@ static int grid_for(long long n, int threads, int cap = 152 * 8)
     return (int)g;
 }
 
-int bin_grid_size(int ncols)
+int bin_grid_size(int ncols, int G)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_bin, kEvalThreads, 0) != cudaSuccess || per_sm < 1) {
+    const void *fn = G == 2 ? (const void *)k_eval_bin<2> : G == 4 ? (const void *)k_eval_bin<4>
+                     : G == 16 ? (const void *)k_eval_bin<16> : (const void *)k_eval_bin<8>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kEvalThreads, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
@@ -1779,7 +1786,8 @@ int bin_grid_size(int ncols)
         cudaGetLastError();
         sms = 152;
     }
-    const long long need = ((long long)ncols + kEvalWarps * kGrpPerWarp - 1) / (kEvalWarps * kGrpPerWarp);
+    const long long cols_per_cta = (long long)kEvalWarps * (32 / G);
+    const long long need = ((long long)ncols + cols_per_cta - 1) / cols_per_cta;
     const long long cap = (long long)sms * per_sm;
     return (int)(need < cap ? need : cap);
 }
@@ -1863,7 +1871,12 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
 #define PROF(k, i) if (prof && e == cudaSuccess) e = cudaEventRecord(p.pev[2 * (k) + (i)], ks[k])
     if (p.n_bin) {
         PROF(0, 0);
-        k_eval_bin<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate);
+        switch (p.bin_G) {
+        case 2: k_eval_bin<2><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate); break;
+        case 4: k_eval_bin<4><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate); break;
+        case 16: k_eval_bin<16><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate); break;
+        default: k_eval_bin<8><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate); break;
+        }
         PROF(0, 1);
     }
     if (p.nb_grid) {

@@ -334,3 +334,18 @@ def test_kernel_timing_api(chap, general_small):
     assert info.grid_bin > 0 and info.grid_nb > 0 and info.bytes_bin > 0 and info.bytes_nb > 0
     chap.chap_bs_profile(bs.h, False)
     bs.close()
+
+
+@pytest.mark.parametrize("n,k,lanes", [(40_000, 4, 2), (3_000, 8, 4), (2_000, 40, 8)])
+def test_binary_lanes_per_column(chap, n, k, lanes):
+    """The binary kernel's lanes per column follow the mean column length; every
+    width is exact against the oracle over a few iterations."""
+    prob = inst.gen_setcover(seed=n + k, n=n, m=n // 2, k=k)
+    bs = chap.BestShift(prob, tenure=10)
+    assert bs.info.bin_lanes == lanes
+    orc = Oracle(prob)
+    for _ in range(3):
+        st = bs.state()
+        assert_exact(bs.best_shift()[:3], oracle_pass(orc, st))
+        bs.run(max_iters=5, stop_at_feasible=0)
+    bs.close()
