@@ -285,7 +285,7 @@ CHAP_API chap_status chap_tabu_run(struct chap_bs *h, const chap_options *opts, 
  *   chain at its first nviol = 0 when stop_at_feasible), graph_iters iterations
  *   per graph replay; res[n_chains] (host, optional) receives per-chain
  *   counters (chap_chain_result), *seconds (optional) the wall time.
- * chap_batch_autotune: times every schedule (lanes per column 4 / 8 / 16 x
+ * chap_batch_autotune: times every schedule (lanes per column 2 / 4 / 8 / 16 x
  *   CTAs per SM 2 / 4 / 8) for `iters` iterations from the initial state, keeps
  *   the fastest (chosen[2] host, optional) and restores the initial state.
  * chap_batch_set_schedule: sets the schedule explicitly.

@@ -349,6 +349,7 @@ cudaError_t launch_eval(const chap_batch *b, int G, int ctas, cudaStream_t st)
     const long long want = (b->dev.total_items + kBThreads / 32 - 1) / (kBThreads / 32);
     const int grid = (int)std::max<long long>(1, std::min<long long>((long long)b->sms * ctas, want));
     switch (G) {
+    case 2: k_batch_eval<2><<<grid, kBThreads, 0, st>>>(b->dev); break;
     case 4: k_batch_eval<4><<<grid, kBThreads, 0, st>>>(b->dev); break;
     case 16: k_batch_eval<16><<<grid, kBThreads, 0, st>>>(b->dev); break;
     default: k_batch_eval<8><<<grid, kBThreads, 0, st>>>(b->dev); break;
@@ -625,14 +626,14 @@ chap_status chap_batch_autotune(chap_batch *b, int32_t iters, int32_t *chosen)
 {
     if (!b || iters < 1) return CHAP_E_INVALID;
     // time every schedule for `iters` iterations from the initial state, keep the fastest
-    const int Gs[3] = {4, 8, 16};
+    const int Gs[4] = {2, 4, 8, 16};
     const int Cs[3] = {2, 4, 8};
     cudaEvent_t a, z;
     BCK(b, cudaEventCreate(&a), "event");
     BCK(b, cudaEventCreate(&z), "event");
     float best_ms = 1e30f;
     int bg = b->G, bc = b->ctas_per_sm;
-    for (int gi = 0; gi < 3; ++gi)
+    for (int gi = 0; gi < 4; ++gi)
         for (int ci = 0; ci < 3; ++ci) {
             chap_status s = upload_state(b);
             if (s != CHAP_OK) { cudaEventDestroy(a); cudaEventDestroy(z); return s; }
@@ -661,7 +662,8 @@ chap_status chap_batch_autotune(chap_batch *b, int32_t iters, int32_t *chosen)
 
 chap_status chap_batch_set_schedule(chap_batch *b, int32_t lanes_per_column, int32_t ctas_per_sm)
 {
-    if (!b || !(lanes_per_column == 4 || lanes_per_column == 8 || lanes_per_column == 16) || ctas_per_sm < 1 ||
+    if (!b || !(lanes_per_column == 2 || lanes_per_column == 4 || lanes_per_column == 8 || lanes_per_column == 16) ||
+        ctas_per_sm < 1 ||
         ctas_per_sm > 32)
         return CHAP_E_INVALID;
     b->G = lanes_per_column;

@@ -173,29 +173,33 @@ __global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16 *w, con
         float xi[kF];
 #pragma unroll
         for (int f = 0; f < kF; ++f) xi[f] = __bfloat162float(x[r * kF + f]);
-        // hidden unit i of the first layer, then its contribution to all 64
-        // pre-activations of the second layer (sums in increasing i)
-        float acc[kH];
-#pragma unroll
-        for (int j = 0; j < kH; ++j) acc[j] = sw[kOffB2 + j];
-#pragma unroll 1
-        for (int i = 0; i < kH; ++i) {
-            float a = sw[kOffB1 + i];
-#pragma unroll
-            for (int f = 0; f < kF; ++f) a = __fmaf_rn(xi[f], sw[kOffW1 + f * kH + i], a);
-            a = fmaxf(a, 0.0f);
-#pragma unroll
-            for (int j = 0; j < kH; j += 4) {
-                const float4 w4 = *reinterpret_cast<const float4 *>(&sw[kOffW2 + i * kH + j]);
-                acc[j] = __fmaf_rn(a, w4.x, acc[j]);
-                acc[j + 1] = __fmaf_rn(a, w4.y, acc[j + 1]);
-                acc[j + 2] = __fmaf_rn(a, w4.z, acc[j + 2]);
-                acc[j + 3] = __fmaf_rn(a, w4.w, acc[j + 3]);
-            }
-        }
+        // the second layer in two halves of 32 outputs (the first layer is
+        // recomputed for each half: fewer live registers, more warps per SM);
+        // every pre-activation sums its terms in increasing i
         float out = sw[kOffB3];
+#pragma unroll 1
+        for (int h = 0; h < kH; h += 32) {
+            float acc[32];
 #pragma unroll
-        for (int j = 0; j < kH; ++j) out = __fmaf_rn(fmaxf(acc[j], 0.0f), sw[kOffW3 + j], out);
+            for (int j = 0; j < 32; ++j) acc[j] = sw[kOffB2 + h + j];
+#pragma unroll 1
+            for (int i = 0; i < kH; ++i) {
+                float a = sw[kOffB1 + i];
+#pragma unroll
+                for (int f = 0; f < kF; ++f) a = __fmaf_rn(xi[f], sw[kOffW1 + f * kH + i], a);
+                a = fmaxf(a, 0.0f);
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 w4 = *reinterpret_cast<const float4 *>(&sw[kOffW2 + i * kH + h + j]);
+                    acc[j] = __fmaf_rn(a, w4.x, acc[j]);
+                    acc[j + 1] = __fmaf_rn(a, w4.y, acc[j + 1]);
+                    acc[j + 2] = __fmaf_rn(a, w4.z, acc[j + 2]);
+                    acc[j + 3] = __fmaf_rn(a, w4.w, acc[j + 3]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) out = __fmaf_rn(fmaxf(acc[j], 0.0f), sw[kOffW3 + h + j], out);
+        }
         y[r] = out;
     }
 }
@@ -356,27 +360,57 @@ __global__ void k_topk_hist(Dev d, Learn L, const float *y, int n, int level, in
 }
 
 // Fix the digit of this level: the largest digit whose count from the top
-// reaches the elements still needed; clears the histogram for the next level.
-__global__ void k_topk_pick(Dev d, Learn L, int level, int k, int n, int gate)
+// reaches the elements still needed (a block-wide suffix scan of the 2048
+// bins); clears the histogram for the next level.
+__global__ void __launch_bounds__(256) k_topk_pick(Dev d, Learn L, int level, int k, int n, int gate)
 {
     if (gate && done_gate(d)) return;
-    if (threadIdx.x == 0) {
-        LearnCtl *c = L.lc;
-        int need = level == 0 ? min(k, n) : c->need;
-        const int nb = level == 2 ? 1024 : 2048;
-        int dig = 0;
-        for (int b = nb - 1; b >= 0; --b) {
-            const int cnt = (int)L.hist[b];
-            if (cnt >= need) { dig = b; break; }
-            need -= cnt;
+    constexpr int PER = 2048 / 256;
+    __shared__ int wsum[8];
+    __shared__ int s_dig, s_need;
+    LearnCtl *c = L.lc;
+    const int need0 = level == 0 ? min(k, n) : c->need;
+    const int nb = level == 2 ? 1024 : 2048;
+    // thread t owns bins [2048 - (t+1) PER, 2048 - t PER): higher bins first
+    const int hi = 2048 - threadIdx.x * PER;
+    int cnt[PER];
+    int tot = 0;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int b = hi - 1 - u;
+        cnt[u] = b < nb ? (int)L.hist[b] : 0;
+        tot += cnt[u];
+    }
+    // exclusive prefix of the per-thread totals in thread order (= from the top)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULLMASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    if (threadIdx.x == 0) { s_dig = 0; s_need = need0; }
+    __syncthreads();
+    int before = incl - tot;
+    for (int w = 0; w < wid; ++w) before += wsum[w];
+    // the thread whose range contains the need0-th element from the top fixes the digit
+    if (before < need0 && before + tot >= need0) {
+        int acc = before;
+        for (int u = 0; u < PER; ++u) {
+            if (acc + cnt[u] >= need0) { s_dig = hi - 1 - u; s_need = need0 - acc; break; }
+            acc += cnt[u];
         }
-        c->need = need;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int dig = s_dig;
+        c->need = s_need;
         const unsigned p = level == 0 ? ((unsigned)dig << 21) : level == 1 ? (c->prefix | ((unsigned)dig << 10))
                                                                            : (c->prefix | (unsigned)dig);
         c->prefix = p;
         if (level == 2) c->thr = p;
     }
-    __syncthreads();
     for (int i = threadIdx.x; i < 2048; i += blockDim.x) L.hist[i] = 0u;
 }
 
