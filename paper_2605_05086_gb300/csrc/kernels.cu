@@ -3,23 +3,21 @@
 // One tabu iteration = best-shift pass (evaluation kernels) -> selection -> apply.
 //
 //  * Binary columns (k_eval_bin): the only move is the flip (Sec. 3.1, "Best
-//    Shift Moves"); its score is a segmented sum of penalties over the column.
-//    G lanes work on one column (G = 4..32 by column length, a whole CTA for very
-//    long columns); each lane keeps four nonzeros in flight, reads them
-//    coalesced inside the column and gathers the row state with one sector.
-//  * Other columns: Algorithm 1 (sort -> scan -> argmax).  Breakpoint entries are
-//    generated from each nonzero (`half_case`, the case table of Algorithm 1);
-//    an a<0 half gives one "pre" entry (its delta counts at t), an a>0 half one
-//    "post" entry (t is a candidate and its delta counts right of t: the two
-//    entries of Algorithm 1 merged).  Entries below l fold into beta, entries
-//    above u are dropped.  The entries of one column are then
-//      - counting-sorted by integer value in shared memory by one warp
-//        (k_eval_hw: integer variables with a domain of at most 256 values), or
-//      - bitonic-sorted in registers by one warp, K entries per lane
-//        (k_eval_sort: up to 256 entries), or
-//      - bitonic-sorted in shared memory by one CTA (k_eval_cta: up to 8192), or
-//      - counting-sorted across many CTAs (k_eval_hist: long integer columns),
-//    prefix-scanned, and reduced to the best admissible candidate.
+//    Shift Moves"); its score is the sum of the penalty changes over the
+//    column.  A group of G lanes (2 .. 16 by mean column length) scores one
+//    column: coalesced reads of the column's nonzeros, one row-state gather per
+//    nonzero, branch-free penalty changes in registers.
+//  * Other columns: Algorithm 1 (sort -> scan -> argmax).  Each normalised half
+//    of a nonzero gives at most one entry (`half_case`, the case table of
+//    Algorithm 1): an a<0 half a "pre" entry (its delta counts at t), an a>0
+//    half a "post" entry (t is a candidate and its delta counts right of t: the
+//    two entries of Algorithm 1 merged); entries left of l fold into beta,
+//    entries right of u are dropped.  Short columns (k_eval_nb, at most 128
+//    entries) place every half by products first and compute exact breakpoints
+//    only for the undecided ones, 32 at a time; their lists are sorted by
+//    group bitonic networks in registers.  Longer columns are bitonic-sorted in
+//    shared memory by one CTA (k_eval_cta, up to 8192 entries) or
+//    counting-sorted across many CTAs (k_eval_hist, long integer columns).
 //  * Every CTA reduces its columns to one candidate; k_select reduces the CTA
 //    candidates (largest score, then lowest variable).
 //  * k_apply walks the chosen column and updates the residuals incrementally
@@ -754,26 +752,6 @@ constexpr int kQCap = 32 + 4 * 32 - 1;      // queued halves per warp: < 32 left
 static_assert(kGrpPerWarp * kGrpStage == kWarpSortMax, "the whole-warp path reuses the group lists");
 using SEnt = SEntry;
 
-// Algorithm 1 scalars of a half whose breakpoint is decided without its key:
-// tight, or certainly left of l (side -1) / right of u (side +1).
-__device__ __forceinline__ void half_acc(bool viol, bool tight, bool apos, int side, long long w, Acc &acc)
-{
-    if (tight) {
-        if (apos) { acc.alpha -= 2 * w; acc.alpha_c += 1; }
-        else { acc.beta -= 2 * w; acc.alpha += 2 * w; acc.beta_c += 1; acc.alpha_c -= 1; }
-        return;
-    }
-    long long D;
-    if (!apos) {
-        if (viol) { acc.beta -= w; acc.alpha += 2 * w; D = w; }
-        else { acc.beta -= 2 * w; acc.beta_c += 1; D = 2 * w; }
-        if (side < 0) { acc.beta += D; acc.beta_c -= 1; }
-    } else {
-        if (viol) { acc.beta += 2 * w; acc.alpha -= 2 * w; acc.beta_c -= 1; D = -w; }
-        else { D = -2 * w; }
-        if (side < 0) { acc.beta += D; acc.beta_c += 1; }
-    }
-}
 
 // Undecided half (operands already negated for the second half of an "=" row):
 //  integral row:      x = r, a (int64);
@@ -795,7 +773,7 @@ struct __align__(16) NbWarp {
 constexpr int kNbSmem = kNbWarps * (int)sizeof(NbWarp);   // dynamic shared memory of k_eval_nb
 
 // Scalars of a decided half as multiples of its weight, branch-free: the case
-// table of Algorithm 1 (as in half_case / half_acc) for index
+// table of Algorithm 1 (as in half_case) for index
 // T*8 + P*4 + V*2 + L (T tight, P a > 0, V violated, L left of l; a half right
 // of u has L = 0), packed as mb + 2 (3 bits), ma / 2 + 1, bc + 1, ac + 1
 // (2 bits each), where beta += mb w, alpha += ma w, beta_c += bc,
