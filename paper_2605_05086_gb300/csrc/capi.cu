@@ -564,8 +564,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         delete h;
         return CHAP_E_CUDA;
     }
-    int64_t apply_need = std::max<int64_t>(m, max_col);
-    pl.apply_blocks = (int)std::min<int64_t>(304, std::max<int64_t>(1, (apply_need + kApplyThreads - 1) / kApplyThreads));
+    pl.apply_blocks = (int)std::min<int64_t>(304, std::max<int64_t>(1, ((int64_t)m + kApplyThreads - 1) / kApplyThreads));
+    pl.apply_move_blocks = (int)std::min<int64_t>(152, std::max<int64_t>(1, ((int64_t)max_col + kApplyMoveThreads - 1) / kApplyMoveThreads));
 
     chap_info &in = h->info;
     in.n = n; in.m = m; in.m_norm = mn;
@@ -573,7 +573,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     in.nnz = p->nnz; in.nnz_int_rows = nnz_int; in.nnz_fp_rows = p->nnz - nnz_int;
     in.eval_blocks = n_tb + n_tn + n_tc + (int)tiles_hist.size();
     in.n_hist_cols = (int)hcols.size();
-    in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + 2;
+    // evaluation kernels (they also select the move), a selection kernel only
+    // when none runs, the move apply and the weight bump
+    in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + (n_bb == 0) + 2;
     // algorithmic bytes of one pass: every nonzero once (row + coefficient),
     // every row state and tolerance once, every active variable's state once.
     int64_t n_act = n - n_fixed;

@@ -186,7 +186,8 @@ struct LaunchPlan {
     int n_hist_tiles;
     int hist_smem;
     int slot_nb, slot_cta;     // first block_best slot of each kernel
-    int apply_blocks;
+    int apply_blocks;          // CTAs of the weight bump
+    int apply_move_blocks;     // CTAs of the move apply (longest column / kApplyMoveThreads)
     cudaStream_t side[3];      // side streams of the non-binary evaluation kernels
     cudaEvent_t ev_fork, ev_join[3];
     // optional timing of the kernels of one pass (outside graph capture):
@@ -226,6 +227,7 @@ constexpr int kHistThreads = 512;
 constexpr int kStaticHistBins = 1 << 16;  // fixed counting-sort scratch: bins (24 B each, 1.5 MiB)
 constexpr int kStaticHistCols = 256;      // and columns
 constexpr int kApplyThreads = 256;
+constexpr int kApplyMoveThreads = 1024;
 constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
 constexpr double kBinG2MaxLen = 6.0;    // mean binary column length up to which 2 lanes score a column
 constexpr int kBinG2MinCols = 32768;    // (and only with this many binary columns: small instances are latency-bound)

@@ -350,6 +350,49 @@ __device__ __forceinline__ bool gated_done(const Dev &d, int gate)
     return gate && *(volatile int *)&d.ctl->done;
 }
 
+// Selection of the pass (Sec. 3.1: the best admissible move over all
+// variables), folded into the evaluation kernels: after writing its candidate
+// slot every CTA takes a ticket, and the CTA that writes the last slot reduces
+// all of them (larger score, then lower variable) into the move record.  All
+// threads of the CTA call it; the ticket is reset for the next pass.
+__device__ void finish_pass(const Dev &d)
+{
+    __shared__ int s_sel;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_sel = atomicAdd(&d.ctl->select_ticket, 1u) == (unsigned)(d.n_block_best - 1);
+    }
+    __syncthreads();
+    if (!s_sel) return;
+    __threadfence();
+    Cand best{0, kNoVar, 0, 0.0};
+    for (int b = threadIdx.x; b < d.n_block_best; b += blockDim.x) {
+        const Cand *p = d.block_best + b;
+        const long long cs = __ldcg(&p->s);
+        const int cv = __ldcg(&p->var);
+        if (cs > 0 && cand_better(cs, cv, best.s, best.var)) best = Cand{cs, cv, __ldcg(&p->dc), __ldcg(&p->xhat)};
+    }
+    best = block_reduce_cand(best);
+    if (threadIdx.x == 0) {
+        Ctl *c = d.ctl;
+        if (best.s > 0 && best.var != kNoVar) {
+            c->mv_var = best.var;
+            c->mv_s = best.s;
+            c->mv_dc = best.dc;
+            c->mv_new = best.xhat;
+            c->mv_old = d.x[best.var];
+        } else {
+            c->mv_var = -1;
+            c->mv_s = 0;
+            c->mv_dc = 0;
+            c->mv_new = 0.0;
+            c->mv_old = 0.0;
+        }
+        c->select_ticket = 0u;
+    }
+}
+
 // ------------------------------------------------------- binary flip scoring
 //
 // The only move of a binary variable is the flip (Sec. 3.1, "Best Shift
@@ -504,6 +547,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, Var
     }
     const Cand b = block_reduce_cand(best);
     if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
+    finish_pass(d);
 }
 
 // ---------------------------------------------- breakpoint generation (Alg. 1)
@@ -1253,6 +1297,7 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
     }
     const Cand bb = block_reduce_cand(best);
     if (threadIdx.x == 0) d.block_best[slot0 + blockIdx.x] = bb;
+    finish_pass(d);
 }
 
 // ------------------------------------------------- CTA bitonic sort (smem)
@@ -1390,6 +1435,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
         finish_column(d, o, c, vb, best);
         d.block_best[slot0 + blockIdx.x] = best;
     }
+    finish_pass(d);
 }
 
 // ------------------------------- multi-CTA counting sort (long integer columns)
@@ -1492,6 +1538,7 @@ __global__ void __launch_bounds__(kHistThreads) k_eval_hist(Dev d, const Tile *t
         d.block_best[hc.slot] = best;
         *ha = HistAcc{0, 0, 0, 0, 0u, 0};
     }
+    finish_pass(d);
 }
 
 // Default of every per-variable output (fixed variables keep it).
@@ -1545,75 +1592,13 @@ __global__ void k_set_move(Dev d, int var, double nv)
 
 // ------------------------------------------------------------------- apply
 
-__global__ void __launch_bounds__(kApplyThreads) k_apply(Dev d, int gate)
+// End of an iteration (one thread): violation count, x and the reverse
+// direction's tabu stamp after a move, counters, best count, feasibility and
+// the run's stop condition.
+__device__ void finish_iteration(const Dev &d, Ctl *c, int var, long long delta)
 {
-    if (gated_done(d, gate)) return;
-    Ctl *c = d.ctl;
-    const int var = c->mv_var;
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int gstride = gridDim.x * blockDim.x;
-    long long local = 0;
-    if (var >= 0) {
-        const double dl = __dsub_rn(c->mv_new, c->mv_old);
-        const long long di = (long long)dl;
-        const int q = d.vpos[var];
-        const int e0 = d.ci_ptr[q], e1 = d.ci_ptr[q + 1];
-        for (int e = e0 + gtid; e < e1; e += gstride) {
-            const int i = d.ci_row[e];
-            const long long a = d.ci_val[e];
-            RowState *p = d.rs + i;
-            const long long r0 = p->r;
-            const long long r1 = r0 + a * di;
-            p->r = r1;
-            local += (long long)(r1 > 0) - (long long)(r0 > 0);
-            if (p->w2 >= 0) local += (long long)(-r1 > 0) - (long long)(-r0 > 0);
-        }
-        const int f0 = d.cf_ptr[q], f1 = d.cf_ptr[q + 1];
-        for (int e = f0 + gtid; e < f1; e += gstride) {
-            const int i = d.cf_row[e];
-            const double a = d.cf_val[e];
-            RowState *p = d.rs + i;
-            const double eps = d.eps[i];
-            const double r1 = __dadd_rn(__longlong_as_double(p->r), __dmul_rn(a, dl));
-            const double m1 = __dsub_rn(eps, r1), m2 = __dadd_rn(eps, r1);
-            local += (long long)dneg(m1) - (long long)dneg(p->m1);
-            if (p->w2 >= 0) local += (long long)dneg(m2) - (long long)dneg(p->m2);
-            p->r = __double_as_longlong(r1);
-            p->m1 = m1;
-            p->m2 = m2;
-        }
-    } else {
-        for (int i = gtid; i < d.m; i += gstride) {
-            RowState *p = d.rs + i;
-            const RowState s = *p;
-            bool v1, v2;
-            if (d.row_int[i]) { v1 = s.r > 0; v2 = -s.r > 0; }
-            else { v1 = dneg(s.m1); v2 = dneg(s.m2); }
-            if (v1) p->w1 = s.w1 + 1;
-            if (s.w2 >= 0 && v2) p->w2 = s.w2 + 1;
-        }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULLMASK, local, off);
-    __shared__ long long red[kApplyThreads / 32];
-    __shared__ int s_last;
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int w = 0; w < kApplyThreads / 32; ++w) t += red[w];
-        if (t) atomicAdd(reinterpret_cast<unsigned long long *>(&c->nviol_delta), (unsigned long long)t);
-        __threadfence();
-        s_last = (atomicAdd(&c->apply_ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    __threadfence();
-    // last CTA: finish the iteration
-    const long long nv = c->nviol + (long long)__ldcg(reinterpret_cast<const long long *>(&c->nviol_delta));
+    const long long nv = c->nviol + delta;
     c->nviol = nv;
-    c->nviol_delta = 0;
-    c->apply_ticket = 0;
     const long long it = c->iter;
     if (var >= 0) {
         d.x[var] = c->mv_new;
@@ -1631,6 +1616,105 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Dev d, int gate)
         c->t_feas_ns = global_ns();
     }
     if ((c->stop_at_feasible && nv == 0) || it + 1 >= c->max_iter) c->done = 1;
+}
+
+// Apply a move: walk the moved column and update its rows' residuals
+// (Sec. 3.1, "Memory Considerations", first point).  The column is split over
+// as many CTAs of kApplyMoveThreads as its length needs (one for the usual
+// columns); the last of them finishes the iteration.
+__global__ void __launch_bounds__(kApplyMoveThreads) k_apply_move(Dev d, int gate)
+{
+    if (gated_done(d, gate)) return;
+    Ctl *c = d.ctl;
+    const int var = c->mv_var;
+    if (var < 0) return;
+    const int q = d.vpos[var];
+    const int e0 = d.ci_ptr[q], e1 = d.ci_ptr[q + 1];
+    const int f0 = d.cf_ptr[q], f1 = d.cf_ptr[q + 1];
+    const int len = (e1 - e0) + (f1 - f0);
+    const int nwork = max(1, (len + kApplyMoveThreads - 1) / kApplyMoveThreads);
+    if ((int)blockIdx.x >= nwork) return;
+    const double dl = __dsub_rn(c->mv_new, c->mv_old);
+    const long long di = (long long)dl;
+    const int stride = nwork * kApplyMoveThreads;
+    long long local = 0;
+    for (int v = blockIdx.x * kApplyMoveThreads + threadIdx.x; v < len; v += stride) {
+        if (v < e1 - e0) {
+            const int e = e0 + v;
+            RowState *p = d.rs + d.ci_row[e];
+            const long long r0 = p->r;
+            const long long r1 = r0 + (long long)d.ci_val[e] * di;
+            p->r = r1;
+            local += (long long)(r1 > 0) - (long long)(r0 > 0);
+            if (p->w2 >= 0) local += (long long)(-r1 > 0) - (long long)(-r0 > 0);
+        } else {
+            const int e = f0 + (v - (e1 - e0));
+            const int i = d.cf_row[e];
+            RowState *p = d.rs + i;
+            const double eps = d.eps[i];
+            const double r1 = __dadd_rn(__longlong_as_double(p->r), __dmul_rn(d.cf_val[e], dl));
+            const double m1 = __dsub_rn(eps, r1), m2 = __dadd_rn(eps, r1);
+            local += (long long)dneg(m1) - (long long)dneg(p->m1);
+            if (p->w2 >= 0) local += (long long)dneg(m2) - (long long)dneg(p->m2);
+            p->r = __double_as_longlong(r1);
+            p->m1 = m1;
+            p->m2 = m2;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULLMASK, local, off);
+    __shared__ long long red[kApplyMoveThreads / 32];
+    __shared__ int s_last;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    long long t = 0;
+    for (int w = 0; w < kApplyMoveThreads / 32; ++w) t += red[w];
+    if (nwork == 1) {
+        finish_iteration(d, c, var, t);
+        return;
+    }
+    if (t) atomicAdd(reinterpret_cast<unsigned long long *>(&c->nviol_delta), (unsigned long long)t);
+    __threadfence();
+    s_last = (atomicAdd(&c->apply_ticket, 1u) == (unsigned)(nwork - 1));
+    if (!s_last) return;
+    __threadfence();
+    const long long tot = (long long)__ldcg(reinterpret_cast<const long long *>(&c->nviol_delta));
+    c->nviol_delta = 0;
+    c->apply_ticket = 0;
+    finish_iteration(d, c, var, tot);
+}
+
+// No admissible positive move: add 1 to the weight of every violated
+// normalised row (the weights of Sec. 3.1's scores); the last CTA finishes the
+// iteration.
+__global__ void __launch_bounds__(kApplyThreads) k_apply_bump(Dev d, int gate)
+{
+    if (gated_done(d, gate)) return;
+    Ctl *c = d.ctl;
+    if (c->mv_var >= 0) return;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gstride = gridDim.x * blockDim.x;
+    for (int i = gtid; i < d.m; i += gstride) {
+        RowState *p = d.rs + i;
+        const RowState s = *p;
+        bool v1, v2;
+        if (d.row_int[i]) { v1 = s.r > 0; v2 = -s.r > 0; }
+        else { v1 = dneg(s.m1); v2 = dneg(s.m2); }
+        if (v1) p->w1 = s.w1 + 1;
+        if (s.w2 >= 0 && v2) p->w2 = s.w2 + 1;
+    }
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(&c->apply_ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    c->apply_ticket = 0;
+    finish_iteration(d, c, -1, 0);
 }
 
 // --------------------------------------------------------- state handling
@@ -1884,18 +1968,23 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
 
 cudaError_t launch_select_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st)
 {
+    // the evaluation kernels select the move themselves (finish_pass); a
+    // kernel is launched only when no evaluation CTA runs
     const bool prof = p.profile && !gate;
     cudaError_t e = prof ? cudaEventRecord(p.pev[8], st) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    k_select<<<1, 1024, 0, st>>>(d, gate);
-    e = cudaGetLastError();
+    if (d.n_block_best == 0) {
+        k_select<<<1, 1024, 0, st>>>(d, gate);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && prof) e = cudaEventRecord(p.pev[9], st);
     return e;
 }
 
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st)
 {
-    k_apply<<<p.apply_blocks, kApplyThreads, 0, st>>>(d, gate);
+    k_apply_move<<<p.apply_move_blocks, kApplyMoveThreads, 0, st>>>(d, gate);
+    k_apply_bump<<<p.apply_blocks, kApplyThreads, 0, st>>>(d, gate);
     return cudaGetLastError();
 }
 
