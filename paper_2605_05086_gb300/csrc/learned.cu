@@ -204,6 +204,96 @@ __global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16 *w, con
     }
 }
 
+// Forward pass with the second layer on the tensor cores: one warp per tile of
+// 16 rows; every lane computes, in FP32 on the CUDA cores, exactly the
+// first-layer activations its A fragments of mma.m16n8k16 need (rows g and
+// g + 8 of the tile, 16 hidden units per 16-wide K chunk), rounds them to BF16,
+// and the warp multiplies the 16 x 64 tile by W2 (64 x 64, BF16 from shared
+// memory) into FP32 accumulators; the output layer is reduced across the four
+// lanes that share a row.  Activations of the first layer are BF16 here
+// (FP32 in k_mlp_forward and in training).
+__global__ void __launch_bounds__(256) k_mlp_forward_tc(const __nv_bfloat16 *w, const __nv_bfloat16 *x, long long n,
+                                                        float *y, const int *done)
+{
+    if (done && *(volatile const int *)done) return;
+    __shared__ float s1[kF * kH + kH];                          // W1, b1
+    __shared__ float s2[kH + kH + 1];                           // b2, w3, b3
+    __shared__ __align__(16) unsigned short sW2t[kH * (kH + 8)];  // W2 transposed, [n][k], padded rows
+    for (int i = threadIdx.x; i < kF * kH + kH; i += blockDim.x) s1[i] = __bfloat162float(w[kOffW1 + i]);
+    for (int i = threadIdx.x; i < 2 * kH + 1; i += blockDim.x) s2[i] = __bfloat162float(w[kOffB2 + i]);
+    const unsigned short *wraw = reinterpret_cast<const unsigned short *>(w);
+    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+        const int k = i / kH, nn = i % kH;                      // W2[k][nn]
+        sW2t[nn * (kH + 8) + k] = wraw[kOffW2 + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long tiles = (n + 15) / 16;
+    for (long long tile = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < tiles;
+         tile += (long long)gridDim.x * (blockDim.x >> 5)) {
+        const long long r0 = tile * 16 + g, r1 = r0 + 8;
+        float x0[kF], x1[kF];
+#pragma unroll
+        for (int f = 0; f < kF; ++f) {
+            x0[f] = r0 < n ? __bfloat162float(x[r0 * kF + f]) : 0.0f;
+            x1[f] = r1 < n ? __bfloat162float(x[r1 * kF + f]) : 0.0f;
+        }
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc) {
+            // A fragment: rows g / g+8, hidden units 16 kc + {2t, 2t+1, 2t+8, 2t+9}
+            unsigned a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 16 * kc + 2 * t + (q >= 2 ? 8 : 0);
+                const float *xr = (q & 1) ? x1 : x0;
+                float v[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float s = s1[kF * kH + c + e];
+#pragma unroll
+                    for (int f = 0; f < kF; ++f) s = __fmaf_rn(xr[f], s1[f * kH + c + e], s);
+                    v[e] = fmaxf(s, 0.0f);
+                }
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(v[0], v[1]);
+                a[q] = *reinterpret_cast<const unsigned *>(&pr);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                // B fragment: k = 16 kc + {2t, 2t+1} and {2t+8, 2t+9}, n = 8 nt + g
+                const unsigned short *bp = sW2t + (8 * nt + g) * (kH + 8) + 16 * kc + 2 * t;
+                const unsigned b0 = *reinterpret_cast<const unsigned *>(bp);
+                const unsigned b1 = *reinterpret_cast<const unsigned *>(bp + 8);
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                    "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+                    : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                    : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+            }
+        }
+        // output layer: rows g (acc[.][0..1]) and g + 8 (acc[.][2..3]), columns 8 nt + 2t (+1)
+        float o0 = 0.0f, o1 = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int c = 8 * nt + 2 * t;
+            o0 = __fmaf_rn(fmaxf(acc[nt][0] + s2[c], 0.0f), s2[kH + c], o0);
+            o0 = __fmaf_rn(fmaxf(acc[nt][1] + s2[c + 1], 0.0f), s2[kH + c + 1], o0);
+            o1 = __fmaf_rn(fmaxf(acc[nt][2] + s2[c], 0.0f), s2[kH + c], o1);
+            o1 = __fmaf_rn(fmaxf(acc[nt][3] + s2[c + 1], 0.0f), s2[kH + c + 1], o1);
+        }
+        o0 += __shfl_xor_sync(FULLMASK, o0, 1);
+        o0 += __shfl_xor_sync(FULLMASK, o0, 2);
+        o1 += __shfl_xor_sync(FULLMASK, o1, 1);
+        o1 += __shfl_xor_sync(FULLMASK, o1, 2);
+        if (t == 0) {
+            if (r0 < n) y[r0] = o0 + s2[2 * kH];
+            if (r1 < n) y[r1] = o1 + s2[2 * kH];
+        }
+    }
+}
+
 // Gradient of the mean squared error over n rows (scale 2/n), accumulated into
 // grad[kNParams] (FP32 atomics, one per parameter and tile), and the sum of
 // squared errors into loss[0].  One CTA of kGradRows threads per tile of rows.
@@ -768,7 +858,8 @@ cudaError_t launch_propose(chap_bs *h, LearnHost *lh, const __nv_bfloat16 *w, in
     const Learn &L = lh->L;
     const int n = d.n;
     k_features<<<grid_n(n, 256), 256, 0, st>>>(d, L, lh->cmax, gate);
-    k_mlp_forward<<<grid_n(n, 256, 152 * 4), 256, 0, st>>>(w, L.feat, n, L.y, gate ? &d.ctl->done : nullptr);
+    k_mlp_forward_tc<<<grid_n((n + 15) / 16 * 32, 256, 152 * 4), 256, 0, st>>>(w, L.feat, n, L.y,
+                                                                             gate ? &d.ctl->done : nullptr);
     for (int level = 0; level < 3; ++level) {
         k_topk_hist<<<grid_n(n, 256, 152 * 2), 256, 0, st>>>(d, L, L.y, n, level, gate);
         k_topk_pick<<<1, 256, 0, st>>>(d, L, level, k, n, gate);

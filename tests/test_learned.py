@@ -148,3 +148,30 @@ def test_training_lowers_the_miss_rate(env):
         rates[name] = r.misses / max(1, r.exact_passes)
         h.close()
     assert rates["trained"] < rates["untrained"], rates
+
+
+def test_tensor_core_forward_in_proposals(env):
+    """The proposal's forward pass runs its second layer on the tensor cores with
+    BF16 first-layer activations: within BF16 rounding of the FP64 oracle."""
+    torch, chap, learn = env
+    prob = inst.gen_setcover(seed=6, n=5000, m=2500, k=8)
+    bs = chap.BestShift(prob, tenure=10)
+    bs.run(max_iters=30, stop_at_feasible=0)
+    chap.chap_bs_refresh_features(bs.h)
+    p = bf16(torch, mlp.init_params(7))
+    w = torch.tensor(p, dtype=torch.float32).to(torch.bfloat16).view(torch.int16).cuda()
+    pred = torch.empty(prob.n, dtype=torch.float32, device="cuda")
+    chap.chap_bs_propose(bs.h, w, 64, None, pred)
+    f = torch.empty((prob.n, 12), dtype=torch.int16, device="cuda")
+    chap.chap_bs_features(bs.h, f, None)
+    x = f.view(torch.bfloat16).to(torch.float64).cpu().numpy()
+    ref = mlp.forward(p, x)
+    got = pred.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 2e-2 * np.max(np.abs(ref)), np.max(np.abs(got - ref))
+    # with the first-layer activations rounded to BF16 as the kernel does, the
+    # rest is FP32 accumulation against FP64: agreement to ~1e-5
+    q = mlp.unpack(p)
+    h1 = bf16(torch, np.maximum(x @ q["W1"] + q["b1"], 0.0))
+    ref16 = np.maximum(h1 @ q["W2"] + q["b2"], 0.0) @ q["w3"] + q["b3"][0]
+    assert np.max(np.abs(got - ref16)) <= 1e-4 * max(1.0, np.max(np.abs(ref16))), np.max(np.abs(got - ref16))
+    bs.close()
