@@ -368,7 +368,7 @@ def main():
     ap.add_argument("--workload", default="general_200k", choices=sorted(inst.WORKLOADS) + ["batch_64x4", "learned_200k", "multiclimb_200k"])
     ap.add_argument("--batch-cap", type=int, default=20000, help="iteration cap per chain (batch_64x4)")
     ap.add_argument("--learned-cap", type=int, default=300000, help="iteration cap (learned_200k)")
-    ap.add_argument("--propose-every", type=int, default=25, help="iterations between proposals (learned_200k)")
+    ap.add_argument("--propose-every", type=int, default=50, help="iterations between proposals (learned_200k)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
