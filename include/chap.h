@@ -269,6 +269,43 @@ CHAP_API chap_status chap_bs_step(struct chap_bs *h, chap_move *out);
 CHAP_API chap_status chap_tabu_run(struct chap_bs *h, const chap_options *opts, chap_tabu_result *result);
 
 /*
+ * Objective cutoff (Sec. 3.2, "Solution Pool": each heuristic imposes the best
+ * known objective as a cutoff constraint so that the search looks for improving
+ * solutions).  Row `row` of the problem, given with sense "<=", holds the
+ * objective: its activity y = a_row . x is the objective value (build it as
+ * c^T x <= B with B at least the largest value over the bounds so that it
+ * starts satisfied, or the incumbent's objective minus delta).  While the
+ * cutoff is on, every iteration that ends with no violated row records the
+ * current x as a solution of objective y (copied to the handle's best-solution
+ * buffer on the device) and tightens the row's rhs to y - delta, which
+ * violates it again; best_nviol restarts from that count (the tightened
+ * problem's record) and chap_tabu_run does not stop at feasibility.
+ * delta: on an integral row an integer in [1, 2^31); on another row any
+ * positive value, raised on the device to at least 4 feas_tol max(1, |y|) so
+ * that the tightened row is violated beyond its tolerance.  row = -1 switches
+ * the cutoff off (delta ignored).  Stream-ordered; a state already feasible
+ * when the cutoff is set is recorded at the end of the next iteration.
+ * CHAP_E_INVALID: row out of range or not a "<=" row, bad delta.
+ */
+CHAP_API chap_status chap_bs_set_cutoff(struct chap_bs *h, int32_t row, double delta);
+
+typedef struct chap_cutoff_info {
+    int64_t solutions;      /* solutions recorded since the cutoff was set */
+    int64_t best_iter;      /* iteration at whose end the best one was recorded (-1: none) */
+    double best_objective;  /* its objective (row activity); NaN when none */
+    double rhs;             /* current rhs of the cutoff row */
+    int32_t row;            /* the cutoff row, -1 when off */
+    int32_t reserved;
+} chap_cutoff_info;
+
+/*
+ * Read the cutoff state (info, host) and optionally the best solution
+ * x_best[n] in `mem` memory (unchanged contents when no solution was
+ * recorded).  Synchronises the stream.
+ */
+CHAP_API chap_status chap_bs_get_cutoff(struct chap_bs *h, chap_cutoff_info *info, double *x_best, int32_t mem);
+
+/*
  * Batched tabu chains (growth path; Sec. 3.1, "Parallel Tabu Search Instances").
  * Many independent chains over several instances advance together: one
  * evaluation launch covers every (chain, 32-column tile), then one apply CTA

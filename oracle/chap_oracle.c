@@ -87,6 +87,8 @@ typedef struct {
     double *nr_eps;     /* 0 on integral rows */
     int32_t *first_nr;  /* first normalised row of original row i */
     int32_t *num_nr;    /* 1 or 2 */
+    uint8_t *row_int;   /* original row i is integral (eps = 0) */
+    double feas_tol;
 } orc_t;
 
 static int is_integer_value(double v) { return isfinite(v) && floor(v) == v; }
@@ -100,6 +102,7 @@ void orc_destroy(orc_t *h)
     free(h->nr_eps);
     free(h->first_nr);
     free(h->num_nr);
+    free(h->row_int);
     free(h);
 }
 
@@ -125,7 +128,9 @@ orc_t *orc_create(int32_t n, int32_t m,
     h->nr_eps = (double *)malloc(sizeof(double) * (size_t)(mn > 0 ? mn : 1));
     h->first_nr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
     h->num_nr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
-    if (!h->nr_orig || !h->nr_sign || !h->nr_rhs || !h->nr_eps || !h->first_nr || !h->num_nr) {
+    h->row_int = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
+    h->feas_tol = feas_tol;
+    if (!h->nr_orig || !h->nr_sign || !h->nr_rhs || !h->nr_eps || !h->first_nr || !h->num_nr || !h->row_int) {
         orc_destroy(h);
         return NULL;
     }
@@ -148,6 +153,7 @@ orc_t *orc_create(int32_t n, int32_t m,
             }
         }
         h->first_nr[i] = k;
+        h->row_int[i] = (uint8_t)integral;
         double eps = integral ? 0.0 : feas_tol * (fabs(rhs[i]) > 1.0 ? fabs(rhs[i]) : 1.0);
         if (sense[i] == ORC_LE || sense[i] == ORC_EQ) {
             h->nr_orig[k] = i; h->nr_sign[k] = 1.0; h->nr_rhs[k] = rhs[i]; h->nr_eps[k] = eps; ++k;
@@ -378,10 +384,87 @@ int32_t orc_max_threads(void)
  * nviol_after[k] the violation count afterwards.  Stops early once nviol == 0
  * when stop_at_feasible is set; returns the number of iterations done.
  */
+/*
+ * Objective cutoff (Sec. 3.2: the best known objective is imposed as a cutoff
+ * constraint so that the search looks for improving solutions).  Original row
+ * `row`, given as "<=", holds the objective; y = its activity at x.  When an
+ * iteration ends with no violated normalised row, x is a solution: y becomes
+ * the best objective, x is copied to x_best and the row's rhs becomes y - d,
+ * d = delta on an integral row and max(delta, 4 feas_tol max(1, |y|))
+ * otherwise (so that the tightened row is violated beyond its tolerance), with
+ * eps recomputed from the new rhs.  The violation record best_nviol restarts
+ * from the count of the tightened problem (a reading: the paper does not say).
+ */
+typedef struct {
+    int32_t row;
+    double delta;
+    double obj;        /* best objective found (out) */
+    int64_t count;     /* solutions recorded (in/out) */
+    int64_t best_iter; /* iteration at whose end the best one was recorded (in/out) */
+    double *x_best;    /* [n] (out) */
+} orc_cut_t;
+
+static void tighten(orc_t *h, orc_cut_t *cut, const double *x, int64_t it)
+{
+    int32_t k = h->first_nr[cut->row];
+    double y = activity(h, k, x);
+    double d = cut->delta;
+    double eps = 0.0;
+    if (!h->row_int[cut->row]) {
+        double dmin = 4.0 * h->feas_tol * (fabs(y) > 1.0 ? fabs(y) : 1.0);
+        if (d < dmin) d = dmin;
+    }
+    double b = y - d;
+    if (!h->row_int[cut->row]) eps = h->feas_tol * (fabs(b) > 1.0 ? fabs(b) : 1.0);
+    h->nr_rhs[k] = b;
+    h->nr_eps[k] = eps;
+    cut->obj = y;
+    cut->count += 1;
+    cut->best_iter = it;
+    memcpy(cut->x_best, x, sizeof(double) * (size_t)h->n);
+}
+
+static int64_t run_loop(orc_t *h, double *x, int32_t *w, int64_t *tabu_inc, int64_t *tabu_dec,
+                        int64_t *iter, int64_t *best_nviol, int32_t tenure, int64_t n_iters,
+                        int32_t stop_at_feasible, orc_cut_t *cut, int32_t *move_var, double *move_val,
+                        int64_t *move_s, int64_t *nviol_after, int32_t nthreads);
+
 int64_t orc_run(const orc_t *h, double *x, int32_t *w, int64_t *tabu_inc, int64_t *tabu_dec,
                 int64_t *iter, int64_t *best_nviol, int32_t tenure, int64_t n_iters,
                 int32_t stop_at_feasible, int32_t *move_var, double *move_val, int64_t *move_s,
                 int64_t *nviol_after, int32_t nthreads)
+{
+    /* without a cutoff the handle is only read */
+    return run_loop((orc_t *)h, x, w, tabu_inc, tabu_dec, iter, best_nviol, tenure, n_iters,
+                    stop_at_feasible, NULL, move_var, move_val, move_s, nviol_after, nthreads);
+}
+
+/*
+ * orc_run under the objective cutoff on original row cut_row (a "<=" row):
+ * never stops at feasibility; cut_obj, cut_count, cut_iter and x_best[n] are
+ * updated at every recorded solution (cut_count and cut_iter carry over from
+ * the caller).  The row's rhs stays tightened in the handle afterwards
+ * (read it with orc_norm_row_info).
+ */
+int64_t orc_run_cutoff(orc_t *h, double *x, int32_t *w, int64_t *tabu_inc, int64_t *tabu_dec,
+                       int64_t *iter, int64_t *best_nviol, int32_t tenure, int64_t n_iters,
+                       int32_t cut_row, double cut_delta, double *cut_obj, int64_t *cut_count,
+                       int64_t *cut_iter, double *x_best, int32_t *move_var, double *move_val,
+                       int64_t *move_s, int64_t *nviol_after, int32_t nthreads)
+{
+    orc_cut_t cut = {cut_row, cut_delta, *cut_obj, *cut_count, *cut_iter, x_best};
+    int64_t done = run_loop(h, x, w, tabu_inc, tabu_dec, iter, best_nviol, tenure, n_iters, 0, &cut,
+                            move_var, move_val, move_s, nviol_after, nthreads);
+    *cut_obj = cut.obj;
+    *cut_count = cut.count;
+    *cut_iter = cut.best_iter;
+    return done;
+}
+
+static int64_t run_loop(orc_t *h, double *x, int32_t *w, int64_t *tabu_inc, int64_t *tabu_dec,
+                        int64_t *iter, int64_t *best_nviol, int32_t tenure, int64_t n_iters,
+                        int32_t stop_at_feasible, orc_cut_t *cut, int32_t *move_var, double *move_val,
+                        int64_t *move_s, int64_t *nviol_after, int32_t nthreads)
 {
     int32_t n = h->n;
     double *xhat = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -412,6 +495,11 @@ int64_t orc_run(const orc_t *h, double *x, int32_t *w, int64_t *tabu_inc, int64_
         *iter += 1;
         int64_t after = orc_residuals(h, x, NULL, NULL);
         if (after < *best_nviol) *best_nviol = after;
+        if (cut && after == 0) {
+            tighten(h, cut, x, *iter);
+            after = orc_residuals(h, x, NULL, NULL);
+            *best_nviol = after;
+        }
         if (move_var) move_var[k] = bj;
         if (move_val) move_val[k] = bj >= 0 ? x[bj] : 0.0;
         if (move_s) move_s[k] = bj >= 0 ? bs : 0;

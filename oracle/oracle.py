@@ -50,6 +50,9 @@ def _load():
     lib.orc_max_threads.restype = C.c_int32
     lib.orc_run.restype = C.c_int64
     lib.orc_run.argtypes = [P, P, P, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, P, P, P, P, C.c_int32]
+    lib.orc_run_cutoff.restype = C.c_int64
+    lib.orc_run_cutoff.argtypes = [P, P, P, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_double,
+                                   P, P, P, P, P, P, P, P, C.c_int32]
     _lib = lib
     return lib
 
@@ -128,6 +131,35 @@ class Oracle:
                                _p(mv), _p(mval), _p(ms), _p(na), int(nthreads))
         state["iter"] = it.value
         state["best_nviol"] = bn.value
+        return dict(var=mv[:done], val=mval[:done], s_half=ms[:done], nviol_after=na[:done])
+
+    def run_cutoff(self, state, tenure, n_iters, cut, nthreads=0):
+        """`run` under the objective cutoff (Sec. 3.2).  `cut` is a dict with the
+        cutoff row `row` and `delta`, updated in place: `obj`, `count`, `best_iter`
+        and `x_best` of the best solution recorded, `rhs` the row's rhs after the
+        run.  Never stops at feasibility."""
+        x = state["x"]; w = state["w"]; ti = state["tabu_inc"]; td = state["tabu_dec"]
+        it = C.c_int64(int(state["iter"]))
+        bn = C.c_int64(int(state["best_nviol"]))
+        obj = C.c_double(float(cut.get("obj", float("nan"))))
+        cnt = C.c_int64(int(cut.get("count", 0)))
+        bi = C.c_int64(int(cut.get("best_iter", -1)))
+        if "x_best" not in cut:
+            cut["x_best"] = np.zeros(self.n)
+        xb = cut["x_best"]
+        mv = np.full(n_iters, -2, np.int32)
+        mval = np.zeros(n_iters)
+        ms = np.zeros(n_iters, np.int64)
+        na = np.zeros(n_iters, np.int64)
+        done = _load().orc_run_cutoff(self.h, _p(x), _p(w), _p(ti), _p(td), C.addressof(it), C.addressof(bn),
+                                      int(tenure), int(n_iters), int(cut["row"]), float(cut["delta"]),
+                                      C.addressof(obj), C.addressof(cnt), C.addressof(bi), _p(xb),
+                                      _p(mv), _p(mval), _p(ms), _p(na), int(nthreads))
+        state["iter"] = it.value
+        state["best_nviol"] = bn.value
+        cut.update(obj=obj.value, count=cnt.value, best_iter=bi.value)
+        orig, _, rhs, _ = self.norm_rows()
+        cut["rhs"] = float(rhs[np.flatnonzero(orig == cut["row"])[0]])
         return dict(var=mv[:done], val=mval[:done], s_half=ms[:done], nviol_after=na[:done])
 
     def initial_state(self, x=None):

@@ -28,7 +28,7 @@ EXPORTED = [
     "chap_batch_create", "chap_batch_destroy", "chap_batch_run", "chap_batch_autotune", "chap_batch_set_schedule",
     "chap_batch_reset", "chap_batch_get_x", "chap_batch_last_error",
     "chap_bs_refresh_features", "chap_bs_features", "chap_bs_propose", "chap_learned_run", "chap_mlp_forward",
-    "chap_mlp_loss_grad", "chap_mlp_adam",
+    "chap_mlp_loss_grad", "chap_mlp_adam", "chap_bs_set_cutoff", "chap_bs_get_cutoff",
 ]
 
 
@@ -60,6 +60,11 @@ class chap_tabu_result(C.Structure):
     _fields_ = [("iters", C.c_int64), ("moves", C.c_int64), ("feasible_iter", C.c_int64),
                 ("final_nviol", C.c_int64), ("best_nviol", C.c_int64), ("seconds", C.c_double),
                 ("time_to_feasible_s", C.c_double), ("objective", C.c_double)]
+
+
+class chap_cutoff_info(C.Structure):
+    _fields_ = [("solutions", C.c_int64), ("best_iter", C.c_int64), ("best_objective", C.c_double),
+                ("rhs", C.c_double), ("row", C.c_int32), ("reserved", C.c_int32)]
 
 
 class chap_info(C.Structure):
@@ -123,6 +128,8 @@ def load(build_if_missing: bool = True):
         "chap_mlp_forward": (I32, [P, P, I64, P, P]),
         "chap_mlp_loss_grad": (I32, [P, P, P, I64, P, P, P]),
         "chap_mlp_adam": (I32, [P, P, P, P, P, I32, C.c_float, P]),
+        "chap_bs_set_cutoff": (I32, [P, I32, D]),
+        "chap_bs_get_cutoff": (I32, [P, P, P, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -275,6 +282,18 @@ def chap_tabu_run(h, opts: chap_options | None = None) -> chap_tabu_result:
     return res
 
 
+def chap_bs_set_cutoff(h, row, delta=1.0):
+    _check(h, load().chap_bs_set_cutoff(h, int(row), float(delta)))
+
+
+def chap_bs_get_cutoff(h, n):
+    """(chap_cutoff_info, x_best as a host array)."""
+    info = chap_cutoff_info()
+    xb = np.zeros(n)
+    _check(h, load().chap_bs_get_cutoff(h, C.byref(info), _ptr(xb), CHAP_MEM_HOST))
+    return info, xb
+
+
 class BestShift:
     """Handle wrapper: BestShift(problem, tenure=10, feas_tol=1e-9, ...)."""
 
@@ -318,6 +337,13 @@ class BestShift:
 
     def step(self):
         return chap_bs_step(self.h)
+
+    def set_cutoff(self, row, delta=1.0):
+        """Objective cutoff on `row` (-1: off); see chap_bs_set_cutoff."""
+        chap_bs_set_cutoff(self.h, row, delta)
+
+    def cutoff(self):
+        return chap_bs_get_cutoff(self.h, self.n)
 
     def run(self, **kw):
         o = chap_options()

@@ -307,6 +307,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
             }
         }
         rint[i] = integral ? 1 : 0;
+        h->row_int.push_back(rint[i]);
+        h->row_le.push_back(p->sense[i] == CHAP_ROW_LE);
         rhs[i] = sign[i] * b;
         eps[i] = integral ? 0.0 : h->opt.feas_tol * std::max(1.0, std::fabs(b));
         if (integral) nnz_int += p->row_ptr[i + 1] - p->row_ptr[i];
@@ -487,6 +489,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     unsigned char *vt_d = dalloc<unsigned char>(h, n);
     double *lb_d = dalloc<double>(h, n), *ub_d = dalloc<double>(h, n), *obj_d = dalloc<double>(h, n);
     d.x = dalloc<double>(h, n);
+    d.x_best = dalloc<double>(h, n);
     d.rs = dalloc<RowState>(h, m);
     d.tabu_inc = dalloc<int>(h, n);
     d.tabu_dec = dalloc<int>(h, n);
@@ -508,7 +511,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     h->t_r = dalloc<double>(h, mn);
     h->t_tabu = dalloc<long long>(h, n);
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && ci_eq_d && cf_eq_d && row_ptr_d && col_idx_d &&
-              row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.rs &&
+              row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.x_best && d.rs &&
               d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
               d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
@@ -840,6 +843,48 @@ chap_status chap_bs_step(chap_bs *h, chap_move *out)
         out->score_half = c.mv_s;
         out->old_value = c.mv_old;
         out->new_value = c.mv_new;
+    }
+    return CHAP_OK;
+}
+
+chap_status chap_bs_set_cutoff(chap_bs *h, int32_t row, double delta)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (row < -1 || row >= h->m) return fail(h, CHAP_E_INVALID, "cutoff row out of range");
+    int integral = 0;
+    if (row >= 0) {
+        if (!h->row_le[row]) return fail(h, CHAP_E_INVALID, "the cutoff row must be a \"<=\" row");
+        integral = h->row_int[row];
+        if (!(delta > 0.0) || !std::isfinite(delta)) return fail(h, CHAP_E_INVALID, "delta must be positive");
+        if (integral && (!is_int_value(delta) || delta >= 2147483648.0))
+            return fail(h, CHAP_E_INVALID, "delta on an integral cutoff row must be an integer in [1, 2^31)");
+    }
+    CK(h, launch_set_cutoff(h->dev, row >= 0, row, integral, row >= 0 ? delta : 0.0, h->opt.feas_tol, h->st),
+       "set cutoff");
+    h->cut_row = row;
+    return CHAP_OK;
+}
+
+chap_status chap_bs_get_cutoff(chap_bs *h, chap_cutoff_info *info, double *x_best, int32_t mem)
+{
+    if (!h) return CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    if (x_best && h->n)
+        CK(h, cudaMemcpyAsync(x_best, h->dev.x_best, sizeof(double) * h->n,
+                              mem == CHAP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st),
+           "copy best solution");
+    chap_status s = read_ctl(h);
+    if (s != CHAP_OK) return s;
+    if (info) {
+        const Ctl &c = *h->h_ctl;
+        info->solutions = c.cut_on ? c.cut_count : 0;
+        info->best_iter = c.cut_on ? c.cut_iter : -1;
+        info->best_objective = c.cut_on ? c.cut_obj : std::nan("");
+        info->rhs = c.cut_on ? c.cut_rhs : std::nan("");
+        info->row = c.cut_on ? c.cut_row : -1;
+        info->reserved = 0;
     }
     return CHAP_OK;
 }

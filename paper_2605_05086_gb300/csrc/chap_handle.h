@@ -18,6 +18,7 @@ struct chap_bs {
     int n = 0, m = 0, m_norm = 0;
     std::vector<double> lb, ub, obj;
     std::vector<uint8_t> vtype, row_eq;
+    std::vector<uint8_t> row_int, row_le;   // integral rows; rows given as "<=" (cutoff candidates)
     std::vector<int> nrow_base;
     std::vector<void *> allocs;
     Dev dev{};
@@ -35,6 +36,7 @@ struct chap_bs {
     bool broken = false;
     bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
     int64_t hist_bins = 0;     // counting-sort bins of the instance
+    int cut_row = -1;          // objective cutoff row (-1: off)
     void *learn = nullptr;     // state of the learned driver (learned.cu), created on first use
     std::string err;
 };

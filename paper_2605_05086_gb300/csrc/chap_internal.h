@@ -74,6 +74,21 @@ struct __align__(16) Ctl {
     unsigned int apply_ticket;
     unsigned int select_ticket;
     int pad;
+    // Objective cutoff (Sec. 3.2, the best known objective imposed as a
+    // constraint): active when cut_on != 0.  Row cut_row holds the objective
+    // as a "<=" row; whenever an iteration ends with no violated row, its
+    // activity is recorded as the best objective and its rhs tightened to that
+    // value minus the required improvement.
+    int cut_on;
+    int cut_row;
+    int cut_int;               // the cutoff row is integral (int64 residual, eps = 0)
+    int pad2;
+    double cut_rhs;            // current rhs of the cutoff row
+    double cut_delta;          // required improvement
+    double cut_tol;            // feasibility tolerance (non-integral row: eps = tol * max(1, |rhs|))
+    double cut_obj;            // objective of the best solution found
+    long long cut_count;       // solutions recorded
+    long long cut_iter;        // iteration that produced the best one
 };
 
 // Work tiles of the best-shift pass.  A tile covers var_list[begin, end).
@@ -135,8 +150,8 @@ struct Dev {
     const long long *row_ptr;
     const int *col_idx;
     const double *row_val;
-    const double *rhs;       // rhs of the first half
-    const double *eps;       // 0 on integral rows
+    double *rhs;             // rhs of the first half (the cutoff row's changes during a run)
+    double *eps;             // 0 on integral rows
     const unsigned char *row_int;
     const int *nrow_base;    // canonical index of the first normalised half of row i
     // variables
@@ -147,6 +162,7 @@ struct Dev {
     RowState *rs;
     int *tabu_inc, *tabu_dec;
     Ctl *ctl;
+    double *x_best;          // copy of x at the last recorded cutoff solution (null: no cutoff)
     // best-shift work
     const int *var_list;     // position -> variable
     const int *vpos;         // variable -> position
@@ -176,7 +192,7 @@ struct VarOut {
 struct LaunchPlan {
     int bin_cols;              // binary columns: positions [0, bin_cols)
     int n_bin;                 // CTAs of the persistent binary kernel (0: no binary column)
-    int bin_G;                 // lanes per binary column (4, 8 or 16, from the mean column length)
+    int bin_G;                 // lanes per binary column (2, 4 or 8, from the mean column length)
     int nb_q0, nb_cols;        // positions of the short non-binary columns (<= kWarpSortMax entries)
     int nb_grid;               // CTAs of the persistent warp-per-column kernel (0: no such column)
     const Tile *tiles_cta;
@@ -213,6 +229,7 @@ cudaError_t launch_set_move(const Dev &d, int var, double new_value, cudaStream_
 cudaError_t launch_residuals(const Dev &d, cudaStream_t st);
 cudaError_t launch_finish_set_state(const Dev &d, long long iter, long long best_nviol, int use_best, cudaStream_t st);
 cudaError_t launch_begin_run(const Dev &d, long long max_iters, int stop_at_feasible, cudaStream_t st);
+cudaError_t launch_set_cutoff(const Dev &d, int on, int row, int integral, double delta, double tol, cudaStream_t st);
 cudaError_t launch_unpack_w(const Dev &d, int *w_norm, cudaStream_t st);
 cudaError_t launch_unpack_r(const Dev &d, double *r_norm, cudaStream_t st);
 cudaError_t launch_tabu_convert(int n, const int *src32, long long *dst64, cudaStream_t st);

@@ -1592,12 +1592,54 @@ __global__ void k_set_move(Dev d, int var, double nv)
 
 // ------------------------------------------------------------------- apply
 
-// End of an iteration (one thread): violation count, x and the reverse
-// direction's tabu stamp after a move, counters, best count, feasibility and
-// the run's stop condition.
-__device__ void finish_iteration(const Dev &d, Ctl *c, int var, long long delta)
+// Objective cutoff (Sec. 3.2): the iteration ended with no violated row, so
+// x is feasible and the cutoff row's activity y = r + b is its objective.  It
+// becomes the best objective and the row's rhs is tightened to y - delta
+// (delta >= 1 and integral on an integral row; on another row at least
+// 4 tol max(1, |y|), so that the tightened row is violated beyond its
+// tolerance).  Returns the cutoff row's violation count after tightening.
+__device__ long long tighten_cutoff(const Dev &d, Ctl *c, long long it)
 {
-    const long long nv = c->nviol + delta;
+    const int i = c->cut_row;
+    RowState *p = d.rs + i;
+    const double b = c->cut_rhs;
+    double y, bn;
+    long long viol;
+    if (c->cut_int) {
+        const long long yl = p->r + (long long)b;
+        const long long bl = yl - (long long)c->cut_delta;
+        p->r = yl - bl;
+        y = (double)yl;
+        bn = (double)bl;
+        viol = p->r > 0;
+    } else {
+        y = __dadd_rn(__longlong_as_double(p->r), b);
+        const double tol = c->cut_tol;
+        const double dmin = __dmul_rn(__dmul_rn(4.0, tol), fmax(1.0, fabs(y)));
+        bn = __dsub_rn(y, fmax(c->cut_delta, dmin));
+        const double rn = __dsub_rn(y, bn);
+        const double eps = __dmul_rn(tol, fmax(1.0, fabs(bn)));
+        p->r = __double_as_longlong(rn);
+        p->m1 = __dsub_rn(eps, rn);
+        p->m2 = __dadd_rn(eps, rn);
+        d.eps[i] = eps;
+        viol = dneg(p->m1);
+    }
+    d.rhs[i] = bn;
+    c->cut_rhs = bn;
+    c->cut_obj = y;
+    c->cut_count += 1;
+    c->cut_iter = it;
+    return viol;
+}
+
+// End of an iteration (one thread): violation count, x and the reverse
+// direction's tabu stamp after a move, counters, best count, feasibility, the
+// objective cutoff and the run's stop condition.  Returns true when a cutoff
+// solution was recorded (the caller's CTA then copies x to x_best).
+__device__ bool finish_iteration(const Dev &d, Ctl *c, int var, long long delta)
+{
+    long long nv = c->nviol + delta;
     c->nviol = nv;
     const long long it = c->iter;
     if (var >= 0) {
@@ -1615,7 +1657,22 @@ __device__ void finish_iteration(const Dev &d, Ctl *c, int var, long long delta)
         c->feasible_iter = it + 1;
         c->t_feas_ns = global_ns();
     }
+    bool snap = false;
+    if (c->cut_on && nv == 0) {
+        // the tightened problem starts a new record of violated rows
+        nv = tighten_cutoff(d, c, it + 1);
+        c->nviol = nv;
+        c->best_nviol = nv;
+        snap = true;
+    }
     if ((c->stop_at_feasible && nv == 0) || it + 1 >= c->max_iter) c->done = 1;
+    return snap;
+}
+
+// Copy of x into x_best by the threads of one CTA (after a cutoff solution).
+__device__ __forceinline__ void snapshot_x(const Dev &d)
+{
+    for (int j = threadIdx.x; j < d.n; j += blockDim.x) d.x_best[j] = d.x[j];
 }
 
 // Apply a move: walk the moved column and update its rows' residuals
@@ -1664,25 +1721,28 @@ __global__ void __launch_bounds__(kApplyMoveThreads) k_apply_move(Dev d, int gat
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULLMASK, local, off);
     __shared__ long long red[kApplyMoveThreads / 32];
-    __shared__ int s_last;
+    __shared__ int s_snap;
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    long long t = 0;
-    for (int w = 0; w < kApplyMoveThreads / 32; ++w) t += red[w];
-    if (nwork == 1) {
-        finish_iteration(d, c, var, t);
-        return;
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < kApplyMoveThreads / 32; ++w) t += red[w];
+        bool last = true;
+        if (nwork > 1) {
+            if (t) atomicAdd(reinterpret_cast<unsigned long long *>(&c->nviol_delta), (unsigned long long)t);
+            __threadfence();
+            last = atomicAdd(&c->apply_ticket, 1u) == (unsigned)(nwork - 1);
+            if (last) {
+                __threadfence();
+                t = (long long)__ldcg(reinterpret_cast<const long long *>(&c->nviol_delta));
+                c->nviol_delta = 0;
+                c->apply_ticket = 0;
+            }
+        }
+        s_snap = last && finish_iteration(d, c, var, t);
     }
-    if (t) atomicAdd(reinterpret_cast<unsigned long long *>(&c->nviol_delta), (unsigned long long)t);
-    __threadfence();
-    s_last = (atomicAdd(&c->apply_ticket, 1u) == (unsigned)(nwork - 1));
-    if (!s_last) return;
-    __threadfence();
-    const long long tot = (long long)__ldcg(reinterpret_cast<const long long *>(&c->nviol_delta));
-    c->nviol_delta = 0;
-    c->apply_ticket = 0;
-    finish_iteration(d, c, var, tot);
+    __syncthreads();
+    if (s_snap) snapshot_x(d);
 }
 
 // No admissible positive move: add 1 to the weight of every violated
@@ -1704,17 +1764,21 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bump(Dev d, int gate)
         if (v1) p->w1 = s.w1 + 1;
         if (s.w2 >= 0 && v2) p->w2 = s.w2 + 1;
     }
-    __shared__ int s_last;
+    __shared__ int s_snap;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = (atomicAdd(&c->apply_ticket, 1u) == gridDim.x - 1);
+        const bool last = atomicAdd(&c->apply_ticket, 1u) == gridDim.x - 1;
+        bool snap = false;
+        if (last) {
+            __threadfence();
+            c->apply_ticket = 0;
+            snap = finish_iteration(d, c, -1, 0);
+        }
+        s_snap = snap;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    __threadfence();
-    c->apply_ticket = 0;
-    finish_iteration(d, c, -1, 0);
+    if (s_snap) snapshot_x(d);
 }
 
 // --------------------------------------------------------- state handling
@@ -1787,10 +1851,28 @@ __global__ void k_finish_set_state(Dev d, long long iter, long long best_nviol, 
     c->error = 0;
 }
 
+// Objective cutoff on row `row` (on = 0 switches it off); the rhs is the
+// row's current one.
+__global__ void k_set_cutoff(Dev d, int on, int row, int integral, double delta, double tol)
+{
+    Ctl *c = d.ctl;
+    c->cut_on = on;
+    c->cut_row = on ? row : 0;
+    c->cut_int = integral;
+    c->cut_rhs = on ? d.rhs[row] : 0.0;
+    c->cut_delta = delta;
+    c->cut_tol = tol;
+    c->cut_obj = __longlong_as_double(0x7ff8000000000000LL);
+    c->cut_count = 0;
+    c->cut_iter = -1;
+}
+
 __global__ void k_begin_run(Dev d, long long max_iters, int stop_at_feasible)
 {
     Ctl *c = d.ctl;
     c->max_iter = c->iter + max_iters;
+    // a run under the objective cutoff continues past every feasible solution
+    if (c->cut_on) stop_at_feasible = 0;
     c->stop_at_feasible = stop_at_feasible;
     c->t_start_ns = global_ns();
     if (c->nviol == 0) { c->feasible_iter = c->iter; c->t_feas_ns = c->t_start_ns; }
@@ -2003,6 +2085,12 @@ cudaError_t launch_residuals(const Dev &d, cudaStream_t st)
 cudaError_t launch_finish_set_state(const Dev &d, long long iter, long long best_nviol, int use_best, cudaStream_t st)
 {
     k_finish_set_state<<<1, 1, 0, st>>>(d, iter, best_nviol, use_best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_cutoff(const Dev &d, int on, int row, int integral, double delta, double tol, cudaStream_t st)
+{
+    k_set_cutoff<<<1, 1, 0, st>>>(d, on, row, integral, delta, tol);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,27 @@ def from_triplets(name, n, m, rows, cols, vals, lb, ub, obj, rhs, vtype, sense, 
     )
 
 
+def with_objective_row(prob, rhs=None):
+    """The problem with one more row, c^T x <= rhs, appended last (index m): the
+    row an objective cutoff tightens.  Default rhs: the largest value of c^T x
+    over the bounds (the row starts satisfied); a variable with c_j = 0 has no
+    entry in it."""
+    c = np.asarray(prob.obj, dtype=np.float64)
+    nzc = np.flatnonzero(c != 0.0)
+    if rhs is None:
+        hi = np.where(c[nzc] > 0, prob.ub[nzc], prob.lb[nzc])
+        rhs = float(np.sum(c[nzc] * hi)) if len(nzc) else 0.0
+        if not np.isfinite(rhs):
+            raise ValueError("an unbounded objective term: give rhs")
+    rows = np.repeat(np.arange(prob.m, dtype=np.int64), np.diff(prob.row_ptr))
+    rows = np.concatenate([rows, np.full(len(nzc), prob.m, dtype=np.int64)])
+    cols = np.concatenate([prob.col_idx.astype(np.int64), nzc.astype(np.int64)])
+    vals = np.concatenate([prob.row_val, c[nzc]])
+    return from_triplets(prob.name + "+obj", prob.n, prob.m + 1, rows, cols, vals, prob.lb, prob.ub, prob.obj,
+                         np.append(prob.rhs, rhs), prob.vtype, np.append(prob.sense, ROW_LE), x0=prob.x0,
+                         meta=dict(prob.meta, cutoff_row=prob.m))
+
+
 def _distinct_segments(rng, lengths, pool_size):
     """For segment s draw lengths[s] distinct values uniformly from range(pool_size).
 
