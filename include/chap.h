@@ -94,7 +94,16 @@ typedef struct chap_problem {
  * while iter < k + 1 + tenure, and symmetrically (default 10).  max_iters: limit
  * of chap_tabu_run (default 1000).  graph_iters: iterations recorded in one CUDA
  * graph replay (default 64).  stop_at_feasible: chap_tabu_run stops at the first
- * iteration that leaves no violated row (default 1).
+ * iteration that leaves no violated row (default 1).  lazy_binary (create time,
+ * default 0): selective re-evaluation of the binary flip scores (the lazy
+ * scheme Sec. 3.1 attributes to earlier GPU heuristics, "Memory
+ * Considerations"): the flip score and violation change of every binary
+ * variable are kept on the device and recomputed only for the variables of
+ * rows whose residual changed (the rows of the moved column); a weight update,
+ * a new state or a tightened cutoff recomputes all of them.  Tabu and
+ * aspiration are applied to the kept values at every iteration, so every
+ * result equals the full pass; the non-binary columns are evaluated in full
+ * at every iteration either way.
  */
 typedef struct chap_options {
     double feas_tol;
@@ -102,7 +111,8 @@ typedef struct chap_options {
     int32_t graph_iters;
     int64_t max_iters;
     int32_t stop_at_feasible;
-    int32_t reserved[7];
+    int32_t lazy_binary;
+    int32_t reserved[6];
 } chap_options;
 
 /* One move.  var = -1 means "no admissible variable has a positive score": the

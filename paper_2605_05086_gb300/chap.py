@@ -48,7 +48,8 @@ class chap_problem(C.Structure):
 
 class chap_options(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("tenure", C.c_int32), ("graph_iters", C.c_int32),
-                ("max_iters", C.c_int64), ("stop_at_feasible", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("max_iters", C.c_int64), ("stop_at_feasible", C.c_int32), ("lazy_binary", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class chap_move(C.Structure):

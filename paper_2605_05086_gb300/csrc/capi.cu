@@ -266,7 +266,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         return vs;
     }
     if (opts) h->opt = *opts; else chap_options_default(&h->opt);
-    if (!(h->opt.feas_tol >= 0.0) || h->opt.tenure < 0 || h->opt.graph_iters < 1) {
+    if (!(h->opt.feas_tol >= 0.0) || h->opt.tenure < 0 || h->opt.graph_iters < 1 ||
+        (h->opt.lazy_binary != 0 && h->opt.lazy_binary != 1)) {
         delete h;
         return CHAP_E_INVALID;
     }
@@ -490,6 +491,13 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     double *lb_d = dalloc<double>(h, n), *ub_d = dalloc<double>(h, n), *obj_d = dalloc<double>(h, n);
     d.x = dalloc<double>(h, n);
     d.x_best = dalloc<double>(h, n);
+    const bool lazy = h->opt.lazy_binary != 0 && bin_cols > 0;
+    if (lazy) {
+        d.lz_s = dalloc<long long>(h, bin_cols);
+        d.lz_dc = dalloc<int>(h, bin_cols);
+        d.lz_mark = dalloc<unsigned>(h, bin_cols);
+        d.lz_list = dalloc<int>(h, bin_cols);
+    }
     d.rs = dalloc<RowState>(h, m);
     d.tabu_inc = dalloc<int>(h, n);
     d.tabu_dec = dalloc<int>(h, n);
@@ -513,7 +521,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && ci_eq_d && cf_eq_d && row_ptr_d && col_idx_d &&
               row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.x_best && d.rs &&
               d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
-              d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu;
+              d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu &&
+              (!lazy || (d.lz_s && d.lz_dc && d.lz_mark && d.lz_list));
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
     if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
     for (int k = 0; k < 3 && ok; ++k)
@@ -553,7 +562,11 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     if (e == cudaSuccess && hist_bins > 0) e = cudaMemsetAsync(d.hbins, 0, sizeof(HBin) * hist_bins, st);
     if (e == cudaSuccess && !hcols.empty()) e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
+    if (e == cudaSuccess && lazy) e = cudaMemsetAsync(d.lz_mark, 0, sizeof(unsigned) * bin_cols, st);
+    if (e == cudaSuccess && lazy) e = launch_lazy_init(d, st);
     LaunchPlan &pl = h->plan;
+    pl.lazy = lazy ? 1 : 0;
+    pl.lazy_mark_blocks = 64;
     pl.bin_cols = bin_cols; pl.n_bin = n_tb; pl.bin_G = bin_G;
     pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn;
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
@@ -578,7 +591,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     in.n_hist_cols = (int)hcols.size();
     // evaluation kernels (they also select the move), a selection kernel only
     // when none runs, the move apply and the weight bump
-    in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + (n_bb == 0) + 2;
+    in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + (n_bb == 0) + 2 +
+                           (lazy ? 2 : 0);   // kept binary scores: the scan and the marking kernel
     // algorithmic bytes of one pass: every nonzero once (row + coefficient),
     // every row state and tolerance once, every active variable's state once.
     int64_t n_act = n - n_fixed;

@@ -89,6 +89,18 @@ struct __align__(16) Ctl {
     double cut_obj;            // objective of the best solution found
     long long cut_count;       // solutions recorded
     long long cut_iter;        // iteration that produced the best one
+    // Selective re-evaluation of the binary flip scores (active when lz_on):
+    // positions marked with the current epoch are queued for re-evaluation;
+    // lz_full asks for all of them.  Each iteration end raises lz_seq and
+    // records the moved variable (lz_var, -1 after a weight update); the
+    // marking kernel handles every sequence number once (lz_done).
+    int lz_on;
+    int lz_full;
+    int lz_count;              // queued positions
+    unsigned lz_epoch;
+    long long lz_seq, lz_done;
+    int lz_var;
+    unsigned lz_ticket;
 };
 
 // Work tiles of the best-shift pass.  A tile covers var_list[begin, end).
@@ -163,6 +175,12 @@ struct Dev {
     int *tabu_inc, *tabu_dec;
     Ctl *ctl;
     double *x_best;          // copy of x at the last recorded cutoff solution (null: no cutoff)
+    // selective binary re-evaluation (null unless enabled): flip score and
+    // violation change of each binary position, epoch marks, queued positions
+    long long *lz_s;
+    int *lz_dc;
+    unsigned *lz_mark;
+    int *lz_list;
     // best-shift work
     const int *var_list;     // position -> variable
     const int *vpos;         // variable -> position
@@ -202,6 +220,8 @@ struct LaunchPlan {
     int n_hist_tiles;
     int hist_smem;
     int slot_nb, slot_cta;     // first block_best slot of each kernel
+    int lazy;                  // binary flips through the kept scores (k_eval_bin_lazy, k_bin_scan)
+    int lazy_mark_blocks;      // CTAs of the marking kernel
     int apply_blocks;          // CTAs of the weight bump
     int apply_move_blocks;     // CTAs of the move apply (longest column / kApplyMoveThreads)
     cudaStream_t side[3];      // side streams of the non-binary evaluation kernels
@@ -230,6 +250,7 @@ cudaError_t launch_residuals(const Dev &d, cudaStream_t st);
 cudaError_t launch_finish_set_state(const Dev &d, long long iter, long long best_nviol, int use_best, cudaStream_t st);
 cudaError_t launch_begin_run(const Dev &d, long long max_iters, int stop_at_feasible, cudaStream_t st);
 cudaError_t launch_set_cutoff(const Dev &d, int on, int row, int integral, double delta, double tol, cudaStream_t st);
+cudaError_t launch_lazy_init(const Dev &d, cudaStream_t st);
 cudaError_t launch_unpack_w(const Dev &d, int *w_norm, cudaStream_t st);
 cudaError_t launch_unpack_r(const Dev &d, double *r_norm, cudaStream_t st);
 cudaError_t launch_tabu_convert(int n, const int *src32, long long *dst64, cudaStream_t st);
@@ -245,6 +266,7 @@ constexpr int kStaticHistBins = 1 << 16;  // fixed counting-sort scratch: bins (
 constexpr int kStaticHistCols = 256;      // and columns
 constexpr int kApplyThreads = 256;
 constexpr int kApplyMoveThreads = 1024;
+constexpr int kLazyMaxRows = 2048;      // longer moved columns re-evaluate every kept binary score
 constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
 constexpr double kBinG2MaxLen = 6.0;    // mean binary column length up to which 2 lanes score a column
 constexpr int kBinG2MinCols = 32768;    // (and only with this many binary columns: small instances are latency-bound)

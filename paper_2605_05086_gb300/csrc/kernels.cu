@@ -500,6 +500,34 @@ __device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, 
     }
 }
 
+// Flip score s and violation change dc of the binary column at position q
+// (all G lanes of its group take part; every lane returns the column sums),
+// with the column's variable j and the flip direction up (0 -> 1).
+template <int G>
+__device__ __forceinline__ void bin_column(const Dev &d, int q, bool live, int sub, int &j, bool &up, long long &s,
+                                           int &dc)
+{
+    const int qq = live ? q : 0;
+    const int ci0 = __ldg(d.ci_ptr + qq), cf0 = __ldg(d.cf_ptr + qq);
+    const int cim = __ldg(d.ci_eq + qq), cfm = __ldg(d.cf_eq + qq);
+    const int ci1 = live ? __ldg(d.ci_ptr + qq + 1) : ci0, cf1 = live ? __ldg(d.cf_ptr + qq + 1) : cf0;
+    j = __ldg(d.var_list + qq);
+    up = __double_as_longlong(d.x[j]) == 0;
+    const int nIs = live ? cim - ci0 : 0, nIe = ci1 - (live ? cim : ci1);
+    const int nFs = live ? cfm - cf0 : 0, nFe = cf1 - (live ? cfm : cf1);
+    s = 0;
+    dc = 0;
+    bin_part<G, false, false>(d, ci0, nIs, groups_max<G>(nIs), sub, up, s, dc);
+    bin_part<G, false, true>(d, cim, nIe, groups_max<G>(nIe), sub, up, s, dc);
+    bin_part<G, true, false>(d, cf0, nFs, groups_max<G>(nFs), sub, up, s, dc);
+    bin_part<G, true, true>(d, cfm, nFe, groups_max<G>(nFe), sub, up, s, dc);
+#pragma unroll
+    for (int o2 = G >> 1; o2 > 0; o2 >>= 1) {
+        s += __shfl_xor_sync(FULLMASK, s, o2);
+        dc += __shfl_xor_sync(FULLMASK, dc, o2);
+    }
+}
+
 template <int G>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, VarOut o, int gate)
 {
@@ -513,25 +541,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, Var
     for (int qd = blockIdx.x * kEvalWarps + warp; qd < nquad; qd += gridDim.x * kEvalWarps) {
         const int q = qd * CPW + g;
         const bool live = q < ncols;
-        const int qq = live ? q : 0;
-        const int ci0 = __ldg(d.ci_ptr + qq), cf0 = __ldg(d.cf_ptr + qq);
-        const int cim = __ldg(d.ci_eq + qq), cfm = __ldg(d.cf_eq + qq);
-        const int ci1 = live ? __ldg(d.ci_ptr + qq + 1) : ci0, cf1 = live ? __ldg(d.cf_ptr + qq + 1) : cf0;
-        const int j = __ldg(d.var_list + qq);
-        const bool up = __double_as_longlong(d.x[j]) == 0;  // flip 0 -> 1
-        const int nIs = live ? cim - ci0 : 0, nIe = ci1 - (live ? cim : ci1);
-        const int nFs = live ? cfm - cf0 : 0, nFe = cf1 - (live ? cfm : cf1);
-        long long s = 0;
-        int dc = 0;
-        bin_part<G, false, false>(d, ci0, nIs, groups_max<G>(nIs), sub, up, s, dc);
-        bin_part<G, false, true>(d, cim, nIe, groups_max<G>(nIe), sub, up, s, dc);
-        bin_part<G, true, false>(d, cf0, nFs, groups_max<G>(nFs), sub, up, s, dc);
-        bin_part<G, true, true>(d, cfm, nFe, groups_max<G>(nFe), sub, up, s, dc);
-#pragma unroll
-        for (int o2 = G >> 1; o2 > 0; o2 >>= 1) {
-            s += __shfl_xor_sync(FULLMASK, s, o2);
-            dc += __shfl_xor_sync(FULLMASK, dc, o2);
-        }
+        int j, dc;
+        bool up;
+        long long s;
+        bin_column<G>(d, q, live, sub, j, up, s, dc);
         if (sub == 0 && live) {
             bool mv = s > 0;
             if (mv) {
@@ -548,6 +561,145 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, Var
     const Cand b = block_reduce_cand(best);
     if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
     finish_pass(d);
+}
+
+// Selective re-evaluation of the binary flips.  k_eval_bin_lazy recomputes the
+// kept score and violation change of the queued positions (all of them when
+// lz_full); k_bin_scan applies tabu and aspiration to the kept values of every
+// binary position, writes the per-CTA candidates of the binary slots and
+// consumes the queue; k_lazy_mark queues the binary positions of every row
+// of the moved column after each iteration.
+template <int G>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_bin_lazy(Dev d, int ncols, int gate)
+{
+    if (gated_done(d, gate)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int CPW = 32 / G;
+    const int g = lane / G, sub = lane & (G - 1);
+    const bool full = d.ctl->lz_full != 0;
+    const int items = full ? ncols : min(d.ctl->lz_count, ncols);
+    const int nquad = (items + CPW - 1) / CPW;
+    for (int qd = blockIdx.x * kEvalWarps + warp; qd < nquad; qd += gridDim.x * kEvalWarps) {
+        const int it = qd * CPW + g;
+        const bool live = it < items;
+        const int q = live ? (full ? it : d.lz_list[it]) : 0;
+        int j, dc;
+        bool up;
+        long long s;
+        bin_column<G>(d, q, live, sub, j, up, s, dc);
+        if (sub == 0 && live) {
+            d.lz_s[q] = s;
+            d.lz_dc[q] = dc;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_bin_scan(Dev d, int ncols, VarOut o, int gate)
+{
+    if (gated_done(d, gate)) return;
+    Ctl *c = d.ctl;
+    const long long iter = c->iter, nviol = c->nviol, bestnv = c->best_nviol;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the queue was consumed by k_eval_bin_lazy
+        c->lz_count = 0;
+        c->lz_full = 0;
+        c->lz_epoch += 1u;
+    }
+    Cand best{0, kNoVar, 0, 0.0};
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ncols; q += gridDim.x * blockDim.x) {
+        const int j = __ldg(d.var_list + q);
+        const bool up = __double_as_longlong(d.x[j]) == 0;
+        const long long s = d.lz_s[q];
+        const int dc = d.lz_dc[q];
+        bool mv = s > 0;
+        if (mv) {
+            const int stamp = up ? d.tabu_inc[j] : d.tabu_dec[j];
+            mv = iter >= (long long)stamp || nviol + (long long)dc < bestnv;
+        }
+        const double xh = up ? 1.0 : 0.0;
+        if (o.xhat) o.xhat[j] = mv ? xh : d.x[j];
+        if (o.s) o.s[j] = mv ? s : 0;
+        if (o.dc) o.dc[j] = mv ? dc : 0;
+        if (mv && cand_better(s, j, best.s, best.var)) best = Cand{s, j, dc, xh};
+    }
+    const Cand b = block_reduce_cand(best);
+    if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
+    finish_pass(d);
+}
+
+// Runs after every apply (not gated by the done flag: the last iteration of
+// a run must be marked as well); acts once per iteration end (lz_seq).  The
+// entries of all rows of the moved column are spread over the whole grid
+// (row offsets in shared memory, a binary search per entry), so a long row
+// does not serialise on one warp.
+__global__ void __launch_bounds__(kEvalThreads) k_lazy_mark(Dev d, int nbin)
+{
+    Ctl *c = d.ctl;
+    const long long seq = c->lz_seq;
+    if (!c->lz_on || seq == c->lz_done) return;
+    const int var = c->lz_var;
+    const unsigned epoch = c->lz_epoch;
+    const int lane = threadIdx.x & 31;
+    __shared__ long long s_off[kLazyMaxRows + 1];   // prefix of the row lengths
+    __shared__ long long s_start[kLazyMaxRows];     // CSR offset of each row
+    int nrows = 0;
+    if (var >= 0 && !c->lz_full) {
+        const int qv = d.vpos[var];
+        const int e0 = d.ci_ptr[qv], f0 = d.cf_ptr[qv];
+        const int nI = d.ci_ptr[qv + 1] - e0, nF = d.cf_ptr[qv + 1] - f0;
+        if (nI + nF > kLazyMaxRows) {
+            // a long column touches most rows: re-evaluate everything instead
+            if (blockIdx.x == 0 && threadIdx.x == 0) c->lz_full = 1;
+        } else {
+            nrows = nI + nF;
+            for (int k = threadIdx.x; k < nrows; k += blockDim.x) {
+                const int i = k < nI ? d.ci_row[e0 + k] : d.cf_row[f0 + (k - nI)];
+                const long long p0 = d.row_ptr[i];
+                s_start[k] = p0;
+                s_off[k + 1] = d.row_ptr[i + 1] - p0;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && nrows > 0) {
+        s_off[0] = 0;
+        for (int k = 1; k <= nrows; ++k) s_off[k] += s_off[k - 1];
+    }
+    __syncthreads();
+    const long long total = nrows > 0 ? s_off[nrows] : 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        const long long g = base + lane;
+        bool fresh = false;
+        int q = 0;
+        if (g < total) {
+            int lo = 0, hi = nrows;   // the row k with s_off[k] <= g < s_off[k + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_off[mid] <= g) lo = mid;
+                else hi = mid;
+            }
+            q = d.vpos[d.col_idx[s_start[lo] + (g - s_off[lo])]];
+            fresh = q < nbin && atomicExch(d.lz_mark + q, epoch) != epoch;
+        }
+        const unsigned bal = __ballot_sync(FULLMASK, fresh);
+        if (bal) {
+            int b0 = 0;
+            if (lane == __ffs(bal) - 1) b0 = atomicAdd(&c->lz_count, __popc(bal));
+            b0 = __shfl_sync(FULLMASK, b0, __ffs(bal) - 1);
+            if (fresh) d.lz_list[b0 + __popc(bal & ((1u << lane) - 1u))] = q;
+        }
+    }
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&c->lz_ticket, 1u) == gridDim.x - 1;
+        if (s_last) {
+            c->lz_ticket = 0;
+            c->lz_done = seq;
+        }
+    }
 }
 
 // ---------------------------------------------- breakpoint generation (Alg. 1)
@@ -1665,6 +1817,13 @@ __device__ bool finish_iteration(const Dev &d, Ctl *c, int var, long long delta)
         c->best_nviol = nv;
         snap = true;
     }
+    if (c->lz_on) {
+        // kept binary scores: the moved column's rows are re-marked; a weight
+        // update or a tightened cutoff row changes too many rows to track
+        c->lz_var = var;
+        if (var < 0 || snap) c->lz_full = 1;
+        c->lz_seq += 1;
+    }
     if ((c->stop_at_feasible && nv == 0) || it + 1 >= c->max_iter) c->done = 1;
     return snap;
 }
@@ -1849,6 +2008,24 @@ __global__ void k_finish_set_state(Dev d, long long iter, long long best_nviol, 
     c->apply_ticket = 0;
     c->select_ticket = 0;
     c->error = 0;
+    if (c->lz_on) {
+        c->lz_full = 1;
+        c->lz_count = 0;
+        c->lz_done = c->lz_seq;
+        c->lz_ticket = 0;
+    }
+}
+
+__global__ void k_lazy_init(Dev d)
+{
+    Ctl *c = d.ctl;
+    c->lz_on = 1;
+    c->lz_full = 1;
+    c->lz_count = 0;
+    c->lz_epoch = 1u;
+    c->lz_seq = 0;
+    c->lz_done = 0;
+    c->lz_ticket = 0;
 }
 
 // Objective cutoff on row `row` (on = 0 switches it off); the rhs is the
@@ -2013,7 +2190,17 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     const bool prof = p.profile && !gate;
     const cudaStream_t ks[4] = {st, p.side[0], p.side[1], p.side[2]};
 #define PROF(k, i) if (prof && e == cudaSuccess) e = cudaEventRecord(p.pev[2 * (k) + (i)], ks[k])
-    if (p.n_bin) {
+    if (p.n_bin && p.lazy) {
+        PROF(0, 0);
+        switch (p.bin_G) {
+        case 2: k_eval_bin_lazy<2><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, gate); break;
+        case 4: k_eval_bin_lazy<4><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, gate); break;
+        case 16: k_eval_bin_lazy<16><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, gate); break;
+        default: k_eval_bin_lazy<8><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, gate); break;
+        }
+        k_bin_scan<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate);
+        PROF(0, 1);
+    } else if (p.n_bin) {
         PROF(0, 0);
         switch (p.bin_G) {
         case 2: k_eval_bin<2><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate); break;
@@ -2067,6 +2254,13 @@ cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cuda
 {
     k_apply_move<<<p.apply_move_blocks, kApplyMoveThreads, 0, st>>>(d, gate);
     k_apply_bump<<<p.apply_blocks, kApplyThreads, 0, st>>>(d, gate);
+    if (p.lazy) k_lazy_mark<<<p.lazy_mark_blocks, kEvalThreads, 0, st>>>(d, p.bin_cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lazy_init(const Dev &d, cudaStream_t st)
+{
+    k_lazy_init<<<1, 1, 0, st>>>(d);
     return cudaGetLastError();
 }
 
