@@ -152,7 +152,7 @@ typedef struct chap_info {
     int64_t bytes_cta;        /* ... of the CTA-sort kernel (long non-integer columns) */
     int64_t bytes_hist;       /* ... of the counting-sort kernel (long integer columns) */
     int32_t bin_lanes;        /* lanes that score one binary column (2, 4, 8 or 16) */
-    int32_t reserved;
+    int32_t nb_lanes;         /* lanes that score one short non-binary column (4 or 8) */
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);

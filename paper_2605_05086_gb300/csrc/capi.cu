@@ -455,7 +455,14 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         }
     }
     const int nb_cols = kind_base[T_NB + 1] - kind_base[T_NB];
-    const int n_tn = nb_cols > 0 ? nb_grid_size(nb_cols) : 0;
+    // lanes per short non-binary column: 4 when the columns are short on average
+    int nb_G = 8;
+    if (nb_cols > 0) {
+        const double mean = (double)((ci_ptr[kind_base[T_NB + 1]] - ci_ptr[kind_base[T_NB]]) +
+                                     (cf_ptr[kind_base[T_NB + 1]] - cf_ptr[kind_base[T_NB]])) / nb_cols;
+        nb_G = mean <= kNbG4MaxLen ? 4 : 8;
+    }
+    const int n_tn = nb_cols > 0 ? nb_grid_size(nb_cols, nb_G) : 0;
     const int bin_cols = kind_base[T_BIN + 1] - kind_base[T_BIN];
     // lanes per binary column: enough for one or two rounds of a mean-length column
     int bin_G = 8;
@@ -568,7 +575,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     pl.lazy = lazy ? 1 : 0;
     pl.lazy_mark_blocks = 64;
     pl.bin_cols = bin_cols; pl.n_bin = n_tb; pl.bin_G = bin_G;
-    pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn;
+    pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn; pl.nb_G = nb_G;
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
     pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);
     pl.slot_nb = n_tb; pl.slot_cta = n_tb + n_tn;
@@ -615,6 +622,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         in.grid_bin = n_tb;
         in.bin_lanes = bin_G;
         in.grid_nb = n_tn;
+        in.nb_lanes = nb_G;
         in.bytes_bin = bin_cols ? kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16) : 0;
         in.bytes_nb = nb_cols ? kernel_bytes(kind_base[T_NB], kind_base[T_NB + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;
         const int ncta = kind_base[T_NB_CTA + 1] - kind_base[T_NB_CTA];

@@ -212,7 +212,8 @@ struct LaunchPlan {
     int n_bin;                 // CTAs of the persistent binary kernel (0: no binary column)
     int bin_G;                 // lanes per binary column (2, 4 or 8, from the mean column length)
     int nb_q0, nb_cols;        // positions of the short non-binary columns (<= kWarpSortMax entries)
-    int nb_grid;               // CTAs of the persistent warp-per-column kernel (0: no such column)
+    int nb_grid;               // CTAs of the persistent short-column kernel (0: no such column)
+    int nb_G;                  // lanes per short non-binary column (4 or 8, from the mean column length)
     const Tile *tiles_cta;
     int n_cta;
     int cta_smem;              // dynamic shared memory of the CTA-sort kernel
@@ -241,7 +242,7 @@ cudaError_t setup_kernel_attributes(const LaunchPlan &p);
 cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc);
 int bin_grid_size(int ncols, int G);  // persistent grids of the binary (G lanes per column) and
                                       // short-column kernels on the current device
-int nb_grid_size(int ncols);
+int nb_grid_size(int ncols, int G);
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st);
 cudaError_t launch_select_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
@@ -272,5 +273,6 @@ constexpr double kBinG2MaxLen = 6.0;    // mean binary column length up to which
 constexpr int kBinG2MinCols = 32768;    // (and only with this many binary columns: small instances are latency-bound)
 constexpr double kBinG4MaxLen = 16.0;   // ... up to which 4 lanes do
 constexpr double kBinG8MaxLen = 1.0e30; // ... up to which 8 lanes do (16 above)
+constexpr double kNbG4MaxLen = 16.0;    // mean short non-binary column length up to which 4 lanes score a column (8 above)
 
 }  // namespace chap

@@ -403,8 +403,6 @@ __device__ void finish_pass(const Dev &d)
 // the row states and add the penalty changes branch-free in registers; a
 // shuffle reduction closes the column.
 
-constexpr int kGrp = 8;                      // lanes per column
-constexpr int kGrpPerWarp = 32 / kGrp;       // columns per warp
 constexpr int kEvalWarps = kEvalThreads / 32;
 
 // Penalty change of a half in weight units for violated-before v0,
@@ -425,7 +423,6 @@ __device__ __forceinline__ int groups_max(int v)
     return v;
 }
 
-__device__ __forceinline__ int quad_max(int v) { return groups_max<kGrp>(v); }
 
 // Flip score terms of one nonzero of an integral row (int64 residual r; a rise
 // of x_j changes r by a; the second half of an "=" row has residual -r and
@@ -921,9 +918,9 @@ __device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, u
 // ------------------------------------------------- short non-binary columns
 //
 // Columns with at most kWarpSortMax breakpoint entries (bounds included).  A
-// group of kGrp = 8 lanes evaluates one column, so one warp holds four columns
-// at a time; a persistent grid takes the warps' column quadruples in a strided
-// order.
+// group of G lanes evaluates one column (G = 8, or 4 when the columns are short
+// on average), so one warp holds 32 / G columns at a time; a persistent grid
+// takes the warps' column groups in a strided order.
 //  1. Classification.  The lanes of a group read the column's nonzeros
 //     coalesced (integral-row part, then the non-integral part), two per lane
 //     in flight, and gather their row states.  Every half is first placed by
@@ -937,36 +934,46 @@ __device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, u
 //     at once (FP64 divisions are slow on this part, so they are never issued
 //     for a single lane), and the entries inside [l, u] are appended to the
 //     column's list in shared memory.
-//  3. Each group sorts its list (bitonic over 8 lanes, 1, 2 or 4 entries per
+//  3. Each group sorts its list (bitonic over G lanes, 1, 2 or 4 entries per
 //     lane), prefix-scans it with shuffles and reduces it to the column's best
-//     admissible candidate.  A column whose list outgrows kGrpStage entries is
+//     admissible candidate.  A column whose list outgrows 4 G entries is
 //     evaluated again by the whole warp with a list of kWarpSortMax entries.
 
 constexpr int kNbWarps = kEvalWarps;
-constexpr int kGrpStage = 4 * kGrp;          // list entries per column on the group path
 constexpr int kQCap = 32 + 4 * 32 - 1;      // queued halves per warp: < 32 left + one round of 4 halves per lane
-static_assert(kGrpPerWarp * kGrpStage == kWarpSortMax, "the whole-warp path reuses the group lists");
 using SEnt = SEntry;
+
+// Shape of the group path for G lanes per column: 32 / G columns per warp,
+// 4 G list entries per column, together the whole-warp list.
+template <int G>
+struct NbGeom {
+    static constexpr int kCols = 32 / G;
+    static constexpr int kStage = 4 * G;
+    static_assert(kCols * kStage == kWarpSortMax, "the whole-warp path reuses the group lists");
+};
 
 
 // Undecided half (operands already negated for the second half of an "=" row):
 //  integral row:      x = r, a (int64);
 //  non-integral row:  x = eps - r (integer variable) or r (continuous), a (double bits),
-// meta = group | row kind << 2 | violated << 3.  A queued half of a continuous
+// meta = group | row kind << 3 | violated << 4.  A queued half of a continuous
 // variable is never "near 0" (|r| <= eps): those are decided by the pre-filter.
 struct __align__(8) QItem {
     long long x, a;
     int w, meta;
 };
 
+template <int G>
 struct __align__(16) NbWarp {
-    SEnt stage[kGrpPerWarp * kGrpStage];
+    SEnt stage[kWarpSortMax];               // the groups' lists, or the whole-warp list
     QItem q[kQCap];                         // ring buffer
-    ColCtx ctx[kGrpPerWarp];
-    long long beta[kGrpPerWarp], alpha[kGrpPerWarp];
-    int beta_c[kGrpPerWarp], alpha_c[kGrpPerWarp], cnt[kGrpPerWarp];
+    ColCtx ctx[32 / G];
+    long long beta[32 / G], alpha[32 / G];
+    int beta_c[32 / G], alpha_c[32 / G], cnt[32 / G];
 };
-constexpr int kNbSmem = kNbWarps * (int)sizeof(NbWarp);   // dynamic shared memory of k_eval_nb
+// dynamic shared memory of k_eval_nb<G>
+template <int G>
+constexpr int nb_smem() { return kNbWarps * (int)sizeof(NbWarp<G>); }
 
 // Scalars of a decided half as multiples of its weight, branch-free: the case
 // table of Algorithm 1 (as in half_case) for index
@@ -1003,10 +1010,10 @@ __device__ __forceinline__ void side_test(float z, float a, float L, float U, fl
 // fp_half after an undecided side test).
 __device__ __forceinline__ void exact_item(const QItem &it, const ColCtx &ci, Acc &acc, Half &h)
 {
-    const bool viol = ((it.meta >> 3) & 1) != 0;
+    const bool viol = ((it.meta >> 4) & 1) != 0;
     bool apos, tight;
     unsigned long long key;
-    if (((it.meta >> 2) & 1) == 0) {
+    if (((it.meta >> 3) & 1) == 0) {
         const long long r = it.x, a = it.a;
         apos = a > 0;
         const long long dd = apos ? floor_div(-r, a) : ceil_div(-r, a);
@@ -1031,13 +1038,14 @@ __device__ __forceinline__ void exact_item(const QItem &it, const ColCtx &ci, Ac
 }
 
 // Exact pass over n <= 32 queued halves starting at ring position head, one per lane.
-__device__ __noinline__ void flush_queue(NbWarp &W, int head, int n, int lane)
+template <int G>
+__device__ __noinline__ void flush_queue(NbWarp<G> &W, int head, int n, int lane)
 {
     if (lane < n) {
         int pos = head + lane;
         if (pos >= kQCap) pos -= kQCap;
         const QItem it = W.q[pos];
-        const int g = it.meta & 3;
+        const int g = it.meta & 7;
         Acc acc{0, 0, 0, 0};
         Half h;
         h.type = 0;
@@ -1048,8 +1056,9 @@ __device__ __noinline__ void flush_queue(NbWarp &W, int head, int n, int lane)
         if (acc.alpha_c) atomicAdd(&W.alpha_c[g], acc.alpha_c);
         if (h.type != 0) {
             const int pos = atomicAdd(&W.cnt[g], 1);
-            if (pos < kGrpStage)
-                W.stage[g * kGrpStage + pos] = SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
+            if (pos < NbGeom<G>::kStage)
+                W.stage[g * NbGeom<G>::kStage + pos] =
+                    SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
         }
     }
     __syncwarp();
@@ -1236,7 +1245,8 @@ struct NbQueue {
 };
 
 // Append the lanes' undecided halves to the warp's ring queue.
-__device__ __forceinline__ void enqueue(NbWarp &W, NbQueue &Q, bool pend, const QItem &it, int lane)
+template <int G>
+__device__ __forceinline__ void enqueue(NbWarp<G> &W, NbQueue &Q, bool pend, const QItem &it, int lane)
 {
     const unsigned bal = __ballot_sync(FULLMASK, pend);
     if (pend) {
@@ -1248,7 +1258,8 @@ __device__ __forceinline__ void enqueue(NbWarp &W, NbQueue &Q, bool pend, const 
 }
 
 // Exact pass over 32 queued halves while 32 are queued.
-__device__ __forceinline__ void drain(NbWarp &W, NbQueue &Q, int lane)
+template <int G>
+__device__ __forceinline__ void drain(NbWarp<G> &W, NbQueue &Q, int lane)
 {
     __syncwarp();
     while (Q.qn >= 32) {
@@ -1264,7 +1275,8 @@ __device__ __forceinline__ void drain(NbWarp &W, NbQueue &Q, int lane)
 // z <= L' aa - [a > 0] and t > u <=> z > H' aa - [a > 0], where L' = lo,
 // H' = hi + 1 (a > 0) or L' = lo - 1, H' = hi (a < 0); |lo a|, |hi a| <= 2^53
 // on integral rows.
-__device__ __forceinline__ void nb_int_half(long long r, int a, int w, bool act, const NbLane &L, NbWarp &W,
+template <int G>
+__device__ __forceinline__ void nb_int_half(long long r, int a, int w, bool act, const NbLane &L, NbWarp<G> &W,
                                             NbQueue &Q, Acc &acc)
 {
     const bool V = r > 0, P = a > 0;
@@ -1275,22 +1287,22 @@ __device__ __forceinline__ void nb_int_half(long long r, int a, int w, bool act,
     const bool left = z <= Lz, right = z > Rz;
     const bool dec = act && (left || right);
     acc_decided(dec ? (((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
-    enqueue(W, Q, act && !dec, QItem{r, (long long)a, w, L.g | ((int)V << 3)}, L.lane);
+    enqueue(W, Q, act && !dec, QItem{r, (long long)a, w, L.g | ((int)V << 4)}, L.lane);
 }
 
 // Both loops below load the next round's row index and coefficient while the
 // current round's row state is gathered (one memory latency per round).
-template <bool EQ>
+template <int G, bool EQ>
 __device__ __forceinline__ void nb_int_part(const Dev &d, int e0, int n, int nmax, int sub, const NbLane &L,
-                                            NbWarp &W, NbQueue &Q, Acc &acc)
+                                            NbWarp<G> &W, NbQueue &Q, Acc &acc)
 {
     const int *rowp = d.ci_row + e0, *valp = d.ci_val + e0;
     bool ok = sub < n;
     int row = ok ? __ldg(rowp + sub) : 0;
     int av = ok ? __ldg(valp + sub) : 1;
-    for (int base = 0; base < nmax; base += kGrp) {
+    for (int base = 0; base < nmax; base += G) {
         const int4 st = ok ? ld_row16(d.rs + row) : make_int4(0, 0, 0, 0);
-        const int vn = base + kGrp + sub;
+        const int vn = base + G + sub;
         const bool okn = vn < n;
         const int rown = okn ? __ldg(rowp + vn) : 0;
         const int avn = okn ? __ldg(valp + vn) : 1;
@@ -1308,8 +1320,9 @@ __device__ __forceinline__ void nb_int_part(const Dev &d, int e0, int n, int nma
 // of the half and mo of the other half.  Integer variable: z = m; continuous:
 // z = -r; the breakpoint is placed by float products with margins, and
 // |r| <= eps makes the half tight wherever t is.
+template <int G>
 __device__ __forceinline__ void nb_fp_half(double r, double a, double m, double mo, int w, bool act,
-                                           const NbLane &L, NbWarp &W, NbQueue &Q, Acc &acc)
+                                           const NbLane &L, NbWarp<G> &W, NbQueue &Q, Acc &acc)
 {
     const bool V = dneg(m), P = !dneg(a);
     const bool T = !L.isint && !V && !dneg(mo);
@@ -1321,24 +1334,24 @@ __device__ __forceinline__ void nb_fp_half(double r, double a, double m, double 
     const bool dec = act && (T || left || right);
     acc_decided(dec ? (((int)T << 3) | ((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
     enqueue(W, Q, act && !dec,
-            QItem{__double_as_longlong(L.isint ? m : r), __double_as_longlong(a), w, L.g | 4 | ((int)V << 3)},
+            QItem{__double_as_longlong(L.isint ? m : r), __double_as_longlong(a), w, L.g | 8 | ((int)V << 4)},
             L.lane);
 }
 
-template <bool EQ>
+template <int G, bool EQ>
 __device__ __forceinline__ void nb_fp_part(const Dev &d, int e0, int n, int nmax, int sub, const NbLane &L,
-                                           NbWarp &W, NbQueue &Q, Acc &acc)
+                                           NbWarp<G> &W, NbQueue &Q, Acc &acc)
 {
     const int *rowp = d.cf_row + e0;
     const double *valp = d.cf_val + e0;
     bool ok = sub < n;
     int row = ok ? __ldg(rowp + sub) : 0;
     double a = ok ? __ldg(valp + sub) : 1.0;
-    for (int base = 0; base < nmax; base += kGrp) {
+    for (int base = 0; base < nmax; base += G) {
         const int4 *p = reinterpret_cast<const int4 *>(d.rs + row);
         const int4 s0 = ok ? __ldg(p) : make_int4(0, 0, 0, 0);
         const int4 s1 = ok ? __ldg(p + 1) : make_int4(0, 0, 0, 0);
-        const int vn = base + kGrp + sub;
+        const int vn = base + G + sub;
         const bool okn = vn < n;
         const int rown = okn ? __ldg(rowp + vn) : 0;
         const double an = okn ? __ldg(valp + vn) : 1.0;
@@ -1352,19 +1365,21 @@ __device__ __forceinline__ void nb_fp_part(const Dev &d, int e0, int n, int nmax
     }
 }
 
+template <int G>
 __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int ncols, VarOut o, int slot0, int gate)
 {
     if (gated_done(d, gate)) return;
     extern __shared__ __align__(16) unsigned char nb_smem[];
-    NbWarp *warps = reinterpret_cast<NbWarp *>(nb_smem);
+    constexpr int CPW = NbGeom<G>::kCols, STG = NbGeom<G>::kStage;
+    NbWarp<G> *warps = reinterpret_cast<NbWarp<G> *>(nb_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane / kGrp, sub = lane & (kGrp - 1);
-    NbWarp &W = warps[warp];
+    const int g = lane / G, sub = lane & (G - 1);
+    NbWarp<G> &W = warps[warp];
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
     Cand best{0, kNoVar, 0, 0.0};
-    const int nquad = (ncols + kGrpPerWarp - 1) / kGrpPerWarp;
+    const int nquad = (ncols + CPW - 1) / CPW;
     for (int qd = blockIdx.x * kNbWarps + warp; qd < nquad; qd += gridDim.x * kNbWarps) {
-        const int cq = qd * kGrpPerWarp + g;
+        const int cq = qd * CPW + g;
         const bool live = cq < ncols;
         int nI, nv, ci0, cf0;
         float Lp, Ln, Up, Un, tolf;
@@ -1395,8 +1410,8 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
                 W.beta[g] = 0; W.alpha[g] = 0; W.beta_c[g] = 0; W.alpha_c[g] = 0;
                 int n = 0;
                 if (live) {
-                    if (dfinite(__ldg(d.lb + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.kl, 0, make_aux(0, 0)};
-                    if (dfinite(__ldg(d.ub + c.j))) W.stage[g * kGrpStage + n++] = SEnt{c.ku, 0, make_aux(0, 0)};
+                    if (dfinite(__ldg(d.lb + c.j))) W.stage[g * STG + n++] = SEnt{c.kl, 0, make_aux(0, 0)};
+                    if (dfinite(__ldg(d.ub + c.j))) W.stage[g * STG + n++] = SEnt{c.ku, 0, make_aux(0, 0)};
                 }
                 W.cnt[g] = n;
             }
@@ -1407,15 +1422,15 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
         const NbLane L{ilo, ihi, Lp, Ln, Up, Un, tolf, fok, isint, g, lane};
         const int cim = live ? __ldg(d.ci_eq + q0 + cq) : ci0, cfm = live ? __ldg(d.cf_eq + q0 + cq) : cf0;
         const int nIs = cim - ci0, nIe = nI - nIs, nFs = cfm - cf0, nFe = (nv - nI) - nFs;
-        nb_int_part<false>(d, ci0, nIs, quad_max(nIs), sub, L, W, Q, acc);
-        nb_int_part<true>(d, cim, nIe, quad_max(nIe), sub, L, W, Q, acc);
-        nb_fp_part<false>(d, cf0, nFs, quad_max(nFs), sub, L, W, Q, acc);
-        nb_fp_part<true>(d, cfm, nFe, quad_max(nFe), sub, L, W, Q, acc);
+        nb_int_part<G, false>(d, ci0, nIs, groups_max<G>(nIs), sub, L, W, Q, acc);
+        nb_int_part<G, true>(d, cim, nIe, groups_max<G>(nIe), sub, L, W, Q, acc);
+        nb_fp_part<G, false>(d, cf0, nFs, groups_max<G>(nFs), sub, L, W, Q, acc);
+        nb_fp_part<G, true>(d, cfm, nFe, groups_max<G>(nFe), sub, L, W, Q, acc);
         const int head = Q.head, qn = Q.qn;
         if (qn > 0) flush_queue(W, head, qn, lane);
         // group sums of the scalars
 #pragma unroll
-        for (int o2 = kGrp >> 1; o2 > 0; o2 >>= 1) {
+        for (int o2 = G >> 1; o2 > 0; o2 >>= 1) {
             acc.beta += __shfl_xor_sync(FULLMASK, acc.beta, o2);
             acc.alpha += __shfl_xor_sync(FULLMASK, acc.alpha, o2);
             acc.beta_c += __shfl_xor_sync(FULLMASK, acc.beta_c, o2);
@@ -1426,25 +1441,25 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
         acc.beta_c += W.beta_c[g];
         acc.alpha_c += W.alpha_c[g];
         const int cnt = W.cnt[g];
-        const bool over = cnt > kGrpStage;
+        const bool over = cnt > STG;
         int cmax = over ? 0 : cnt;
 #pragma unroll
-        for (int o2 = 16; o2 >= kGrp; o2 >>= 1) cmax = max(cmax, __shfl_xor_sync(FULLMASK, cmax, o2));
+        for (int o2 = 16; o2 >= G; o2 >>= 1) cmax = max(cmax, __shfl_xor_sync(FULLMASK, cmax, o2));
         {
             const ColCtx &c = W.ctx[g];
-            const SEnt *list = W.stage + g * kGrpStage;
+            const SEnt *list = W.stage + g * STG;
             VCand vb;
-            if (cmax <= kGrp) vb = group_sort_scan<1, kGrp>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
-            else if (cmax <= 2 * kGrp) vb = group_sort_scan<2, kGrp>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
-            else vb = group_sort_scan<4, kGrp>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
+            if (cmax <= G) vb = group_sort_scan<1, G>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
+            else if (cmax <= 2 * G) vb = group_sort_scan<2, G>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
+            else vb = group_sort_scan<4, G>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
             if (sub == 0 && live && !over) finish_column(d, o, c, vb, best);
         }
         __syncwarp();
         unsigned ovf = __ballot_sync(FULLMASK, sub == 0 && live && over);
         while (ovf) {
-            const int gg = (__ffs(ovf) - 1) / kGrp;
+            const int gg = (__ffs(ovf) - 1) / G;
             ovf &= ovf - 1;
-            column_warp(d, o, q0 + qd * kGrpPerWarp + gg, W.stage, iter, nviol, bestnv, best);
+            column_warp(d, o, q0 + qd * CPW + gg, W.stage, iter, nviol, bestnv, best);
         }
     }
     const Cand bb = block_reduce_cand(best);
@@ -2113,13 +2128,15 @@ int bin_grid_size(int ncols, int G)
     return (int)(need < cap ? need : cap);
 }
 
-int nb_grid_size(int ncols)
+int nb_grid_size(int ncols, int G)
 {
     // one resident wave: every SM holds as many CTAs as fit, and no CTA is
     // launched without a column for each of its warps to start with
     int per_sm = 0;
-    if (cudaFuncSetAttribute(k_eval_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, kNbSmem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_nb, kEvalThreads, kNbSmem) != cudaSuccess || per_sm < 1) {
+    const void *fn = G == 4 ? (const void *)k_eval_nb<4> : (const void *)k_eval_nb<8>;
+    const int smem = G == 4 ? nb_smem<4>() : nb_smem<8>();
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kEvalThreads, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
@@ -2128,7 +2145,8 @@ int nb_grid_size(int ncols)
         cudaGetLastError();
         sms = 152;
     }
-    const long long need = ((long long)ncols + kNbWarps * kGrpPerWarp - 1) / (kNbWarps * kGrpPerWarp);
+    const long long cols_per_cta = (long long)kNbWarps * (32 / G);
+    const long long need = ((long long)ncols + cols_per_cta - 1) / cols_per_cta;
     const long long cap = (long long)sms * per_sm;
     return (int)(need < cap ? need : cap);
 }
@@ -2168,7 +2186,9 @@ cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc)
 cudaError_t setup_kernel_attributes(const LaunchPlan &p)
 {
     cudaError_t e = cudaSuccess;
-    if (p.nb_grid > 0) e = cudaFuncSetAttribute(k_eval_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, kNbSmem);
+    if (p.nb_grid > 0)
+        e = p.nb_G == 4 ? cudaFuncSetAttribute(k_eval_nb<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb_smem<4>())
+                        : cudaFuncSetAttribute(k_eval_nb<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb_smem<8>());
     if (e == cudaSuccess && p.cta_smem > 0)
         e = cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, p.cta_smem);
     if (e == cudaSuccess && p.hist_smem > 0)
@@ -2212,7 +2232,10 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     }
     if (p.nb_grid) {
         PROF(1, 0);
-        k_eval_nb<<<p.nb_grid, kEvalThreads, kNbSmem, p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
+        if (p.nb_G == 4)
+            k_eval_nb<4><<<p.nb_grid, kEvalThreads, nb_smem<4>(), p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
+        else
+            k_eval_nb<8><<<p.nb_grid, kEvalThreads, nb_smem<8>(), p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
         PROF(1, 1);
     }
     if (p.n_cta) {

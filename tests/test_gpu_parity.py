@@ -309,13 +309,17 @@ def _breakpoint_columns(seed, lengths, dom=200, eq_frac=0.2):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_list_lengths_group_and_warp_paths(chap, seed):
-    """Columns whose lists take every sort of the short-column kernel (8, 16 and
-    32 entries per group, the whole-warp path for lists longer than a group
-    holds) and the counting sort, plus a partial last column quadruple."""
-    prob = _breakpoint_columns(seed, [3, 7, 12, 20, 30, 45, 60, 100, 5])
+@pytest.mark.parametrize("lengths,lanes", [([3, 7, 12, 20, 30, 45, 60, 100, 5], 8),
+                                           ([1, 2, 3, 5, 7, 9, 12, 15, 18, 25, 4, 2, 3, 6, 11], 4)])
+def test_list_lengths_group_and_warp_paths(chap, seed, lengths, lanes):
+    """Columns whose lists take every sort of the short-column kernel (G, 2 G
+    and 4 G entries per group of G lanes, the whole-warp path for lists longer
+    than a group holds) and the counting sort, plus a partial last group of
+    columns; G = 8 for long columns on average, 4 for short ones."""
+    prob = _breakpoint_columns(seed, lengths)
     orc = Oracle(prob)
     bs = chap.BestShift(prob, tenure=3)
+    assert bs.info.nb_lanes == lanes
     for it in range(4):
         st = bs.state()
         assert_exact(bs.best_shift()[:3], oracle_pass(orc, st))
