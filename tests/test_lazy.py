@@ -142,3 +142,20 @@ def test_lazy_option_validated(chap):
     b = chap.BestShift(tiny, tenure=3)
     assert a.info.launches_per_step == b.info.launches_per_step
     same_outputs(a, b)
+
+
+def test_lazy_under_the_learned_loop(chap):
+    """The learned loop (proposals between exact passes) over a handle with kept
+    binary scores takes the moves of the same loop without them: the marks of
+    the proposal iterations accumulate until the next exact pass."""
+    torch = pytest.importorskip("torch")
+    from paper_2605_05086_gb300 import learn
+    prob = inst.gen_setcover(seed=8, n=3000, m=1500, k=8)
+    w = learn.to_bf16_bits(torch.tensor(learn.init_params(3), device="cuda"))
+    a = chap.BestShift(prob, tenure=7, lazy_binary=1)
+    b = chap.BestShift(prob, tenure=7)
+    ra = chap.chap_learned_run(a.h, w, topk=128, exact_every=9, propose_every=2, max_iters=400, stop_at_feasible=False)
+    rb = chap.chap_learned_run(b.h, w, topk=128, exact_every=9, propose_every=2, max_iters=400, stop_at_feasible=False)
+    assert (ra.iters, ra.misses, ra.exact_passes) == (rb.iters, rb.misses, rb.exact_passes)
+    same_state(a, b)
+    same_outputs(a, b)
