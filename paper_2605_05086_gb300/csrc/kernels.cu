@@ -18,11 +18,18 @@
 //    group bitonic networks in registers.  Longer columns are bitonic-sorted in
 //    shared memory by one CTA (k_eval_cta, up to 8192 entries) or
 //    counting-sorted across many CTAs (k_eval_hist, long integer columns).
-//  * Every CTA reduces its columns to one candidate; k_select reduces the CTA
-//    candidates (largest score, then lowest variable).
-//  * k_apply walks the chosen column and updates the residuals incrementally
-//    (Sec. 3.1, "Memory Considerations", first point); when no positive move
-//    exists it adds 1 to the weight of every violated normalised row.
+//  * Every CTA reduces its columns to one candidate; the CTA that writes the
+//    last candidate slot reduces them all into the move (finish_pass: largest
+//    score, then lowest variable; k_select only when no evaluation CTA runs).
+//  * k_apply_move walks the chosen column and updates the residuals
+//    incrementally (Sec. 3.1, "Memory Considerations", first point); when no
+//    positive move exists k_apply_bump adds 1 to the weight of every violated
+//    normalised row.  The CTA that ends the iteration (finish_iteration) also
+//    tightens the objective cutoff row when the iteration ends feasible
+//    (Sec. 3.2) and copies x to the best solution.
+//  * Optional kept binary scores (k_eval_bin_lazy, k_bin_scan, k_lazy_mark):
+//    the flips of the binaries in the moved column's rows are re-evaluated,
+//    tabu and aspiration are applied to the kept values of all of them.
 //
 // Exactness: integral rows use int64 residuals and integer arithmetic only;
 // non-integral rows keep r, eps - r and eps + r (double, explicit
