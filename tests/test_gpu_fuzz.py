@@ -131,3 +131,50 @@ def test_fuzz_states_and_steps(chap, seed):
     if dyadic:
         compare(bs, orc)
     bs.close()
+
+
+def random_fp_instance(seed):
+    """General coefficients (N(0,1) rows mixed with integer rows), tolerance 1e-9."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(10, 50))
+    m = int(rng.integers(8, 50))
+    vt = rng.choice(np.array([B, I, C], dtype=np.uint8), size=n, p=[0.4, 0.35, 0.25])
+    lb = np.where(vt == B, 0.0, rng.integers(-3, 2, size=n).astype(np.float64))
+    ub = np.where(vt == B, 1.0, lb + rng.integers(1, 30, size=n))
+    xs = np.where(vt == C, lb + rng.random(n) * (ub - lb), np.floor(lb + rng.random(n) * (ub - lb + 1)))
+    xs = np.minimum(xs, ub)
+    rows, cols, vals = [], [], []
+    for i in range(m):
+        js = rng.choice(n, size=int(rng.integers(1, min(7, n) + 1)), replace=False)
+        integral = rng.random() < 0.5
+        for j in sorted(js.tolist()):
+            rows.append(i); cols.append(j)
+            vals.append(float(rng.integers(-9, 10) or 1) if integral else float(rng.normal()))
+    ax = np.zeros(m)
+    for r, c, v in zip(rows, cols, vals):
+        ax[r] += v * xs[c]
+    sense = rng.choice(np.array([0, 1, 2], dtype=np.uint8), size=m, p=[0.4, 0.4, 0.2])
+    slack = rng.random(m) * 2.0
+    rhs = np.where(sense == 0, ax + slack, np.where(sense == 1, ax - slack, ax))
+    x0 = np.clip(np.zeros(n), lb, ub)
+    return inst.from_triplets(f"fuzzfp_{seed}", n, m, rows, cols, vals, lb, ub, rng.integers(1, 5, size=n),
+                              rhs, vt, sense, x0=x0)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_fuzz_general_coefficients_within_tolerance(chap, seed):
+    """Non-dyadic rows: scores and violation changes equal, shifts within 1e-9
+    relative; a case inside the tolerance window around xbar may differ (no
+    more than one variable per pass)."""
+    prob = random_fp_instance(seed)
+    orc = Oracle(prob)
+    bs = chap.BestShift(prob, tenure=3)
+    for _ in range(4):
+        st = bs.state()
+        g = bs.best_shift()
+        o = orc.best_shift(st["x"], st["w"], st["tabu_inc"], st["tabu_dec"], st["iter"], st["nviol"], st["best_nviol"])
+        xok = np.abs(g[0] - o[0]) <= 1e-9 * np.maximum(1.0, np.abs(o[0]))
+        bad = np.nonzero(~(xok & (g[1] == o[1]) & (g[2] == o[2])))[0]
+        assert len(bad) <= 1, [(int(k), g[0][k], o[0][k], int(g[1][k]), int(o[1][k])) for k in bad[:6]]
+        bs.run(max_iters=5, stop_at_feasible=0)
+    bs.close()
