@@ -56,7 +56,7 @@ enum {
     CHAP_E_CUDA = 3,        /* a CUDA runtime call failed */
     CHAP_E_TIMEOUT = 4,     /* a bounded device-side wait ran out */
     CHAP_E_STATE = 5,       /* call not valid in the handle's current state */
-    CHAP_E_UNSUPPORTED = 6  /* valid input outside what this build handles */
+    CHAP_E_UNSUPPORTED = 6  /* valid input outside what the library handles */
 };
 
 enum { CHAP_VAR_BIN = 0, CHAP_VAR_INT = 1, CHAP_VAR_CONT = 2 };
