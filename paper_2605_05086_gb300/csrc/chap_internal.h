@@ -74,6 +74,10 @@ struct __align__(16) Ctl {
     unsigned int apply_ticket;
     unsigned int select_ticket;
     int pad;
+    // Largest admissible score found so far in the current pass (0 between
+    // passes): a lower bound of the move's score, against which the
+    // short-column kernel skips the sort of columns that cannot reach it.
+    long long pass_best;
     // Objective cutoff (Sec. 3.2, the best known objective imposed as a
     // constraint): active when cut_on != 0.  Row cut_row holds the objective
     // as a "<=" row; whenever an iteration ends with no violated row, its

@@ -397,6 +397,7 @@ __device__ void finish_pass(const Dev &d)
             c->mv_old = 0.0;
         }
         c->select_ticket = 0u;
+        c->pass_best = 0;
     }
 }
 
@@ -563,7 +564,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, Var
         }
     }
     const Cand b = block_reduce_cand(best);
-    if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
+    if (threadIdx.x == 0) {
+        d.block_best[blockIdx.x] = b;
+        if (b.s > 0) atomicMax(&d.ctl->pass_best, b.s);
+    }
     finish_pass(d);
 }
 
@@ -627,7 +631,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_bin_scan(Dev d, int ncols, Var
         if (mv && cand_better(s, j, best.s, best.var)) best = Cand{s, j, dc, xh};
     }
     const Cand b = block_reduce_cand(best);
-    if (threadIdx.x == 0) d.block_best[blockIdx.x] = b;
+    if (threadIdx.x == 0) {
+        d.block_best[blockIdx.x] = b;
+        if (b.s > 0) atomicMax(&d.ctl->pass_best, b.s);
+    }
     finish_pass(d);
 }
 
@@ -1449,17 +1456,46 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
         acc.alpha_c += W.alpha_c[g];
         const int cnt = W.cnt[g];
         const bool over = cnt > STG;
-        int cmax = over ? 0 : cnt;
+        // Bound: no candidate of the column scores above beta + (its positive
+        // deltas) + max(alpha, 0).  A column whose bound is not positive, or
+        // is below an admissible score already found in this pass, cannot
+        // give the move, so its list is not sorted (exact; only when no
+        // per-variable output is asked for).
+        bool prune = false;
+        if (!(o.xhat || o.s || o.dc)) {
+            const long long found = *reinterpret_cast<volatile const long long *>(&d.ctl->pass_best);
+            long long pos = 0;
+            if (!over)
+                for (int e = sub; e < cnt; e += G) {
+                    const long long D = W.stage[g * STG + e].del;
+                    pos += D > 0 ? D : 0;
+                }
+#pragma unroll
+            for (int o2 = G >> 1; o2 > 0; o2 >>= 1) pos += __shfl_xor_sync(FULLMASK, pos, o2);
+            const long long bound = acc.beta + pos + (acc.alpha > 0 ? acc.alpha : 0);
+            prune = !over && (bound <= 0 || bound < found);
+        }
+        int cmax = (over || prune) ? 0 : cnt;
 #pragma unroll
         for (int o2 = 16; o2 >= G; o2 >>= 1) cmax = max(cmax, __shfl_xor_sync(FULLMASK, cmax, o2));
         {
             const ColCtx &c = W.ctx[g];
             const SEnt *list = W.stage + g * STG;
-            VCand vb;
-            if (cmax <= G) vb = group_sort_scan<1, G>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
-            else if (cmax <= 2 * G) vb = group_sort_scan<2, G>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
-            else vb = group_sort_scan<4, G>(c, acc, list, over ? 0 : cnt, nviol, bestnv);
-            if (sub == 0 && live && !over) finish_column(d, o, c, vb, best);
+            VCand vb{0, 0ull, 0, 0};
+            const int cn = (over || prune) ? 0 : cnt;
+            if (cmax == 0) {
+                // every column of the warp pruned, overflowing or without entries
+            } else if (cmax <= G) {
+                vb = group_sort_scan<1, G>(c, acc, list, cn, nviol, bestnv);
+            } else if (cmax <= 2 * G) {
+                vb = group_sort_scan<2, G>(c, acc, list, cn, nviol, bestnv);
+            } else {
+                vb = group_sort_scan<4, G>(c, acc, list, cn, nviol, bestnv);
+            }
+            if (sub == 0 && live && !over) {
+                finish_column(d, o, c, vb, best);
+                if (best.s > 0) atomicMax(&d.ctl->pass_best, best.s);
+            }
         }
         __syncwarp();
         unsigned ovf = __ballot_sync(FULLMASK, sub == 0 && live && over);
@@ -2030,6 +2066,7 @@ __global__ void k_finish_set_state(Dev d, long long iter, long long best_nviol, 
     c->apply_ticket = 0;
     c->select_ticket = 0;
     c->error = 0;
+    c->pass_best = 0;
     if (c->lz_on) {
         c->lz_full = 1;
         c->lz_count = 0;

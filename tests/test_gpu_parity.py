@@ -353,3 +353,20 @@ def test_binary_lanes_per_column(chap, n, k, lanes):
         assert_exact(bs.best_shift()[:3], oracle_pass(orc, st))
         bs.run(max_iters=5, stop_at_feasible=0)
     bs.close()
+
+
+@pytest.mark.parametrize("which", ["general", "skewed"])
+def test_pass_without_outputs_selects_the_full_pass_move(chap, general_small, which):
+    """A pass that returns only the move skips the list sort of short columns
+    whose score bound cannot reach an admissible score already found; the move
+    must be the one of the full pass (which returns every variable's result)."""
+    prob = general_small if which == "general" else \
+        inst.gen_skewed(seed=7, n=100_000, m=50_000, n_dense=2, dense_len=5_000)
+    bs = chap.BestShift(prob, tenure=10)
+    for it in range(12):
+        full = bs.best_shift()[3]
+        _, _, _, quick = chap.chap_bs_best_shift(bs.h, want_vars=False)
+        assert (quick.var, quick.score_half, quick.dnviol, quick.new_value) == \
+            (full.var, full.score_half, full.dnviol, full.new_value), it
+        bs.run(max_iters=25, stop_at_feasible=0)
+    bs.close()
