@@ -884,7 +884,6 @@ chap_status chap_bs_set_cutoff(chap_bs *h, int32_t row, double delta)
     }
     CK(h, launch_set_cutoff(h->dev, row >= 0, row, integral, row >= 0 ? delta : 0.0, h->opt.feas_tol, h->st),
        "set cutoff");
-    h->cut_row = row;
     return CHAP_OK;
 }
 

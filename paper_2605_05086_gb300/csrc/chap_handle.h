@@ -36,7 +36,6 @@ struct chap_bs {
     bool broken = false;
     bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
     int64_t hist_bins = 0;     // counting-sort bins of the instance
-    int cut_row = -1;          // objective cutoff row (-1: off)
     void *learn = nullptr;     // state of the learned driver (learned.cu), created on first use
     std::string err;
 };
