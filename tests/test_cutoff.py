@@ -260,3 +260,48 @@ def test_cutoff_arguments(chap):
     bs.set_cutoff(-1)
     info, _ = bs.cutoff()
     assert info.row == -1
+
+
+def _golden_problem():
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cutoff_example.json")))
+    pr = g["problem"]
+    rows, cols, vals = [], [], []
+    for i, r in enumerate(pr["rows"]):
+        for j, a in r["coefs"]:
+            rows.append(i); cols.append(j); vals.append(float(a))
+    prob = inst.from_triplets("cutoff_golden", pr["n"], len(pr["rows"]), rows, cols, vals, np.array(pr["lb"], float),
+                              np.array(pr["ub"], float), np.array(pr["obj"], float),
+                              np.array([r["rhs"] for r in pr["rows"]], float), np.array(pr["vtype"], np.uint8),
+                              np.array([r["sense"] for r in pr["rows"]], np.uint8), x0=np.array(pr["x0"], float))
+    return g, pr, prob
+
+
+def test_oracle_cutoff_hand_derived_example():
+    """The oracle's cutoff run against a trajectory worked out by hand
+    (tests/golden/cutoff_example.json)."""
+    g, pr, prob = _golden_problem()
+    orc = Oracle(prob)
+    st = orc.initial_state()
+    cut = dict(row=pr["cutoff_row"], delta=float(pr["delta"]))
+    tr = orc.run_cutoff(st, pr["tenure"], len(g["steps"]), cut)
+    assert tr["var"].tolist() == [s["var"] for s in g["steps"]]
+    assert tr["s_half"].tolist() == [s["s_half"] for s in g["steps"]]
+    assert tr["nviol_after"].tolist() == g["nviol_after"]
+    assert (cut["count"], cut["best_iter"], cut["obj"], cut["rhs"]) == \
+        (g["solutions"], g["best_iter"], g["best_objective"], g["rhs_after"])
+    assert cut["x_best"].tolist() == g["x_best"]
+    assert st["w"].tolist() == g["w_after"]
+
+
+@pytest.mark.gpu
+def test_cutoff_hand_derived_example_on_gpu(chap):
+    g, pr, prob = _golden_problem()
+    bs = chap.BestShift(prob, tenure=pr["tenure"])
+    bs.set_cutoff(pr["cutoff_row"], float(pr["delta"]))
+    got = [(mv.var, mv.score_half) for mv in (bs.step() for _ in g["steps"])]
+    assert got == [(s["var"], s["s_half"]) for s in g["steps"]]
+    info, xb = bs.cutoff()
+    assert (info.solutions, info.best_iter, info.best_objective, info.rhs) == \
+        (g["solutions"], g["best_iter"], g["best_objective"], g["rhs_after"])
+    assert xb.tolist() == g["x_best"] and bs.state()["w"].tolist() == g["w_after"]
