@@ -229,3 +229,33 @@ def test_thread_count_does_not_change_trajectory():
     for k in ta:
         assert np.array_equal(ta[k], tb[k])
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["w"], b["w"])
+
+
+def test_tabu_trajectory_hand_derived():
+    """Tabu stamps (iter + 1 + tenure), aspiration and weight updates over seven
+    iterations against a trajectory worked out by hand
+    (tests/golden/tabu_example.json): a stamp one iteration short would take
+    the move at iteration 5 instead of 6."""
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "tabu_example.json")))
+    pr = g["problem"]
+    rows, cols, vals = [], [], []
+    for i, r in enumerate(pr["rows"]):
+        for j, a in r["coefs"]:
+            rows.append(i); cols.append(j); vals.append(float(a))
+    prob = inst.from_triplets("tabu_golden", pr["n"], len(pr["rows"]), rows, cols, vals, np.array(pr["lb"], float),
+                              np.array(pr["ub"], float), np.ones(pr["n"]),
+                              np.array([r["rhs"] for r in pr["rows"]], float), np.array(pr["vtype"], np.uint8),
+                              np.array([r["sense"] for r in pr["rows"]], np.uint8), x0=np.array(pr["x0"], float))
+    orc = Oracle(prob)
+    st = orc.initial_state()
+    tr = orc.run(st, pr["tenure"], len(g["steps"]), stop_at_feasible=False)
+    assert tr["var"].tolist() == [s["var"] for s in g["steps"]]
+    assert tr["s_half"].tolist() == [s["s_half"] for s in g["steps"]]
+    for k, s in enumerate(g["steps"]):
+        if s["var"] >= 0:
+            assert tr["val"][k] == s["val"], k
+    assert tr["nviol_after"].tolist() == g["nviol_after"]
+    assert st["x"].tolist() == g["x_after"] and st["w"].tolist() == g["w_after"]
+    assert st["tabu_inc"].tolist() == g["tabu_inc_after"] and st["tabu_dec"].tolist() == g["tabu_dec_after"]
+    assert st["best_nviol"] == g["best_nviol_after"]
