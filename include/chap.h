@@ -165,7 +165,11 @@ CHAP_API void chap_options_default(chap_options *opts);
  * inconsistent CSR/CSC, unsorted or out-of-range indices, NaN or infinite
  * coefficients or rhs, l > u, binary bounds outside {0,1}, fractional integer
  * bounds; CHAP_E_UNSUPPORTED when more than 2^31 - 1 nonzeros or rows, or a
- * continuous column whose breakpoint list cannot be sorted on chip.
+ * continuous column whose breakpoint list cannot be sorted on chip;
+ * CHAP_E_OOM when a device allocation fails (everything allocated so far is
+ * released).  Testing hook: with the environment variable
+ * CHAP_FAIL_ALLOC_AFTER=N set, the device allocation after the first N of
+ * this call fails.
  * Ref: Sec. 3.1 (problem form, normalisation), Algorithm 1 (inputs).
  */
 CHAP_API chap_status chap_bs_create(const chap_problem *prob, const chap_options *opts,

@@ -11,6 +11,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -52,6 +53,8 @@ template <class T>
 T *dalloc(chap_bs *h, size_t count)
 {
     void *p = nullptr;
+    if (h->fail_allocs_after == 0) return nullptr;   // injected allocation failure (testing)
+    if (h->fail_allocs_after > 0) --h->fail_allocs_after;
     if (count == 0) count = 1;
     if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
@@ -266,6 +269,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         return vs;
     }
     if (opts) h->opt = *opts; else chap_options_default(&h->opt);
+    if (const char *f = std::getenv("CHAP_FAIL_ALLOC_AFTER")) h->fail_allocs_after = std::atol(f);
     if (!(h->opt.feas_tol >= 0.0) || h->opt.tenure < 0 || h->opt.graph_iters < 1 ||
         (h->opt.lazy_binary != 0 && h->opt.lazy_binary != 1)) {
         delete h;

@@ -36,6 +36,7 @@ struct chap_bs {
     bool broken = false;
     bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
     int64_t hist_bins = 0;     // counting-sort bins of the instance
+    long fail_allocs_after = -1; // device allocations left before an injected failure (-1: none)
     void *learn = nullptr;     // state of the learned driver (learned.cu), created on first use
     std::string err;
 };

@@ -115,3 +115,25 @@ def test_kernel_boundary_columns(chap, n_rows, vtype):
         assert (bs.info.n_hist_cols == 1) == expect_long
     bs.close()
     check(chap, prob, steps=4)
+
+
+def test_create_releases_everything_on_allocation_failure(chap, monkeypatch):
+    """An injected device-allocation failure at several points of chap_bs_create
+    returns CHAP_E_OOM and leaves no device memory behind; without it the same
+    problem builds and runs."""
+    import torch
+    prob = inst.gen_general(seed=2, n=3000, m=1500, len_cap=200)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for n_ok in (0, 1, 7, 20, 33):
+        monkeypatch.setenv("CHAP_FAIL_ALLOC_AFTER", str(n_ok))
+        with pytest.raises(chap.ChapError) as e:
+            chap.BestShift(prob, tenure=5)
+        assert e.value.status == chap.CHAP_E_OOM
+    monkeypatch.delenv("CHAP_FAIL_ALLOC_AFTER")
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
+    bs = chap.BestShift(prob, tenure=5)
+    bs.run(max_iters=20, stop_at_feasible=0)
+    assert bs.state()["iter"] == 20
+    bs.close()
