@@ -112,7 +112,10 @@ typedef struct chap_options {
     int64_t max_iters;
     int32_t stop_at_feasible;
     int32_t lazy_binary;
-    int32_t reserved[6];
+    int32_t static_scratch_only; /* create time, default 0: see chap_bs_best_shift_static_scratch */
+    int32_t shard_rank;          /* create time: column shard of this handle (see chap_bs_move_record) */
+    int32_t shard_count;         /* create time, default 0 or 1: the handle evaluates every column */
+    int32_t reserved[3];
 } chap_options;
 
 /* One move.  var = -1 means "no admissible variable has a positive score": the
@@ -153,6 +156,8 @@ typedef struct chap_info {
     int64_t bytes_hist;       /* ... of the counting-sort kernel (long integer columns) */
     int32_t bin_lanes;        /* lanes that score one binary column (2, 4, 8 or 16) */
     int32_t nb_lanes;         /* lanes that score one short non-binary column (4 or 8) */
+    int32_t n_long_cols;      /* columns on the multi-CTA merge-sort path (lists over 8192 entries) */
+    int32_t reserved;
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);
@@ -164,8 +169,7 @@ CHAP_API void chap_options_default(chap_options *opts);
  * cudaStream_t (NULL = legacy default stream).  Returns CHAP_E_INVALID for
  * inconsistent CSR/CSC, unsorted or out-of-range indices, NaN or infinite
  * coefficients or rhs, l > u, binary bounds outside {0,1}, fractional integer
- * bounds; CHAP_E_UNSUPPORTED when more than 2^31 - 1 nonzeros or rows, or a
- * continuous column whose breakpoint list cannot be sorted on chip;
+ * bounds; CHAP_E_UNSUPPORTED when more than 2^31 - 1 nonzeros or rows;
  * CHAP_E_OOM when a device allocation fails (everything allocated so far is
  * released).  Testing hook: with the environment variable
  * CHAP_FAIL_ALLOC_AFTER=N set, the device allocation after the first N of
@@ -187,8 +191,9 @@ CHAP_API chap_status chap_bs_info(const struct chap_bs *h, chap_info *info);
  * selection (never inside chap_tabu_run's graph).  chap_bs_kernel_ms then
  * synchronises the handle's stream and writes the durations of the last
  * profiled pass in milliseconds: ms[0] binary flips, ms[1] short non-binary
- * columns, ms[2] CTA-sorted columns, ms[3] counting-sorted columns, ms[4]
- * selection (0 for a kernel the instance does not launch).  ms has 5
+ * columns, ms[2] CTA-sorted columns and long lists (merge sort), ms[3]
+ * counting-sorted columns, ms[4] selection (0 for a kernel the instance does
+ * not launch).  ms has 5
  * elements (host).  CHAP_E_STATE when no profiled pass ran since enabling.
  */
 CHAP_API chap_status chap_bs_profile(struct chap_bs *h, int32_t enable);
@@ -255,19 +260,62 @@ CHAP_API chap_status chap_bs_apply(struct chap_bs *h, int32_t var, double new_va
 /*
  * Same pass and outputs as chap_bs_best_shift, but the long integer columns
  * sorted by the multi-CTA counting sort use a fixed scratch compiled into the
- * library (a file-scope device array: 65536 bins, 256 columns) instead of the
- * handle's own scratch.  No counterpart in the paper: it is for callers that
- * must not hold device memory per handle for this scratch (many handles under
- * a fixed device-memory budget).  The call allocates nothing; the first call
- * on a device resolves the scratch's address (do it before any stream
- * capture).  The scratch starts at zero and every pass leaves it at zero; it is
- * shared by all handles of the process, so passes through it must not overlap
- * (same or different handles, any streams): overlapping calls race.
- * CHAP_E_UNSUPPORTED (with a message) when the instance needs more than 65536
- * bins or 256 columns.  Arguments as chap_bs_best_shift.
+ * library (a file-scope device array: 65536 bins, 256 columns, 1.5 MiB held by
+ * every GPU that loads the library until the process exits) instead of the
+ * handle's own scratch.  No counterpart in the paper.  It is for callers that
+ * cannot give each handle device memory for this scratch: many handles kept
+ * under a fixed device-memory budget, or a memory pool that owns the device
+ * and hands out nothing per handle.  Create such handles with
+ * chap_options.static_scratch_only = 1: they then hold no counting-sort
+ * scratch of their own, and every other call that runs a pass
+ * (chap_bs_best_shift, chap_bs_step, chap_tabu_run, chap_bs_refresh_features,
+ * chap_learned_run) returns CHAP_E_STATE when the instance has counting-sorted
+ * columns (n_hist_cols > 0).  The call allocates nothing; its first call on a
+ * device resolves the scratch's address with that device current (make it
+ * before any stream capture); concurrent first calls from several host threads
+ * are serialised.  The scratch starts at zero and every pass leaves it at
+ * zero; it is shared by all handles of the process, so passes through it must
+ * not overlap on the GPU (same or different handles, any streams): overlapping
+ * calls race.  CHAP_E_UNSUPPORTED (with a message) when the instance needs more
+ * than 65536 bins or 256 columns.  Arguments as chap_bs_best_shift.
  */
 CHAP_API chap_status chap_bs_best_shift_static_scratch(struct chap_bs *h, double *xhat, int64_t *score_half,
                                                        int32_t *dnviol, chap_move *best, int32_t mem);
+
+/*
+ * Column-sharded pass over several GPUs (Sec. 3.1: the pass is independent per
+ * variable, so its columns can be split; one GPU per process, see DESIGN).
+ * A handle created with chap_options.shard_count = K > 1 and shard_rank = k
+ * stores the whole instance (every column, for the incremental update of the
+ * apply) and replicated state, but its best-shift pass evaluates only shard k:
+ * every K-th column of each column class (round robin over the class order).
+ * Its chap_bs_best_shift then gives the shard's best move (per-variable
+ * outputs of the other columns: the incumbent, score 0).  One iteration of the
+ * sharded search: every rank runs chap_bs_best_shift (device outputs or none),
+ * writes its move record with chap_bs_move_record, the K records are
+ * exchanged (an all-gather of 32 bytes per rank, e.g. NCCL), and every rank
+ * calls chap_bs_apply_records with all K records in rank order: the record of
+ * the largest score wins (ties: the lowest variable; no positive score on any
+ * rank: the weight update), so every rank applies the same move and the state
+ * stays replicated.  chap_bs_step, chap_tabu_run and the learned driver
+ * return CHAP_E_STATE on a sharded handle.
+ *
+ * chap_bs_move_record: the move selected by the handle's last pass into rec
+ *   (host or device memory as mem says; stream-ordered, synchronises for host).
+ * chap_bs_apply_records: reduces recs[0..k) (host or device; 1 <= k <= 1024)
+ *   on the device and applies the winner like chap_bs_apply (or the weight
+ *   update).  CHAP_E_INVALID for a host record naming a variable out of range.
+ */
+typedef struct chap_move_record {
+    int64_t score_half;    /* <= 0: no move on this shard */
+    int32_t var;           /* -1 when no move */
+    int32_t dnviol;
+    double new_value;
+    double old_value;
+} chap_move_record;
+
+CHAP_API chap_status chap_bs_move_record(struct chap_bs *h, chap_move_record *rec, int32_t mem);
+CHAP_API chap_status chap_bs_apply_records(struct chap_bs *h, const chap_move_record *recs, int32_t k, int32_t mem);
 
 /* One full tabu iteration: best-shift pass, selection, then apply or weight update.
  * out (host, optional) receives the move taken. */

@@ -29,6 +29,7 @@ EXPORTED = [
     "chap_batch_reset", "chap_batch_get_x", "chap_batch_last_error",
     "chap_bs_refresh_features", "chap_bs_features", "chap_bs_propose", "chap_learned_run", "chap_mlp_forward",
     "chap_mlp_loss_grad", "chap_mlp_adam", "chap_bs_set_cutoff", "chap_bs_get_cutoff",
+    "chap_bs_move_record", "chap_bs_apply_records",
 ]
 
 
@@ -49,12 +50,21 @@ class chap_problem(C.Structure):
 class chap_options(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("tenure", C.c_int32), ("graph_iters", C.c_int32),
                 ("max_iters", C.c_int64), ("stop_at_feasible", C.c_int32), ("lazy_binary", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("static_scratch_only", C.c_int32), ("shard_rank", C.c_int32), ("shard_count", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class chap_move(C.Structure):
     _fields_ = [("var", C.c_int32), ("dnviol", C.c_int32), ("score_half", C.c_int64),
                 ("old_value", C.c_double), ("new_value", C.c_double)]
+
+
+class chap_move_record(C.Structure):
+    _fields_ = [("score_half", C.c_int64), ("var", C.c_int32), ("dnviol", C.c_int32),
+                ("new_value", C.c_double), ("old_value", C.c_double)]
+
+
+MOVE_RECORD_BYTES = 32
 
 
 class chap_tabu_result(C.Structure):
@@ -75,7 +85,8 @@ class chap_info(C.Structure):
                 ("bytes_per_pass", C.c_int64), ("eval_blocks", C.c_int32), ("n_hist_cols", C.c_int32),
                 ("launches_per_step", C.c_int32), ("grid_bin", C.c_int32), ("grid_nb", C.c_int32),
                 ("bytes_bin", C.c_int64), ("bytes_nb", C.c_int64), ("bytes_cta", C.c_int64),
-                ("bytes_hist", C.c_int64), ("bin_lanes", C.c_int32), ("nb_lanes", C.c_int32)]
+                ("bytes_hist", C.c_int64), ("bin_lanes", C.c_int32), ("nb_lanes", C.c_int32),
+                ("n_long_cols", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -130,6 +141,8 @@ def load(build_if_missing: bool = True):
         "chap_mlp_loss_grad": (I32, [P, P, P, I64, P, P, P]),
         "chap_mlp_adam": (I32, [P, P, P, P, P, I32, C.c_float, P]),
         "chap_bs_set_cutoff": (I32, [P, I32, D]),
+        "chap_bs_move_record": (I32, [P, P, I32]),
+        "chap_bs_apply_records": (I32, [P, P, I32, I32]),
         "chap_bs_get_cutoff": (I32, [P, P, P, I32]),
     }
     for name, (res, args) in sig.items():
@@ -352,6 +365,73 @@ class BestShift:
         for k, v in kw.items():
             setattr(o, k, v)
         return chap_tabu_run(self.h, o)
+
+
+def chap_bs_move_record(h, rec=None, mem=CHAP_MEM_HOST):
+    """The move of the handle's last pass: a chap_move_record (host), or written
+    into `rec` (a device buffer of 32 bytes, e.g. a torch uint8 tensor) when
+    mem=CHAP_MEM_DEVICE."""
+    if mem == CHAP_MEM_HOST:
+        r = chap_move_record()
+        _check(h, load().chap_bs_move_record(h, C.byref(r), mem))
+        return r
+    _check(h, load().chap_bs_move_record(h, _ptr(rec), mem))
+    return rec
+
+
+def chap_bs_apply_records(h, recs, k=None, mem=CHAP_MEM_HOST):
+    """Apply the winner of k move records: a ctypes array of chap_move_record
+    (host) or a device buffer of k * 32 bytes (mem=CHAP_MEM_DEVICE)."""
+    if mem == CHAP_MEM_HOST:
+        k = len(recs) if k is None else k
+        _check(h, load().chap_bs_apply_records(h, recs, int(k), mem))
+    else:
+        _check(h, load().chap_bs_apply_records(h, _ptr(recs), int(k), mem))
+
+
+def exchange_records(local, world, group=None):
+    """All-gather of the ranks' 32-byte move records: returns the world's
+    records in rank order as one uint8 tensor of world * 32 bytes on local's
+    device (NCCL for CUDA tensors; gloo takes host tensors)."""
+    import torch
+    import torch.distributed as dist
+    out = torch.empty(world * MOVE_RECORD_BYTES, dtype=torch.uint8, device=local.device)
+    parts = list(out.split(MOVE_RECORD_BYTES))
+    dist.all_gather(parts, local.contiguous(), group=group)
+    return out
+
+
+class ShardedSearch:
+    """One rank of the column-sharded tabu search: a handle that evaluates every
+    world-th column, and the exchange of the 32-byte move records.
+
+    exchange(local) must return the world's records in rank order as a device
+    uint8 tensor of world * 32 bytes (an all-gather: NCCL across GPUs); the
+    default is exchange_records on the current process group.  Every rank then
+    applies the same winning move."""
+
+    def __init__(self, prob, rank, world, stream=None, exchange=None, **opts):
+        import torch
+        self.bs = BestShift(prob, stream=stream, shard_rank=int(rank), shard_count=int(world), **opts)
+        self.rank, self.world = int(rank), int(world)
+        self.rec = torch.zeros(MOVE_RECORD_BYTES, dtype=torch.uint8, device="cuda")
+        self.exchange = exchange or (lambda local: exchange_records(local, self.world))
+
+    def pass_record(self):
+        """The shard's pass and its move record (device)."""
+        lib = load()
+        _check(self.bs.h, lib.chap_bs_best_shift(self.bs.h, None, None, None, None, CHAP_MEM_DEVICE))
+        chap_bs_move_record(self.bs.h, self.rec, CHAP_MEM_DEVICE)
+        return self.rec
+
+    def apply(self, records):
+        chap_bs_apply_records(self.bs.h, records, self.world, CHAP_MEM_DEVICE)
+
+    def step(self):
+        self.apply(self.exchange(self.pass_record()))
+
+    def close(self):
+        self.bs.close()
 
 
 class chap_chain_result(C.Structure):

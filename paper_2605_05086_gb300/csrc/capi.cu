@@ -214,6 +214,24 @@ cudaError_t bs_pass(chap_bs *h, const VarOut &o)
 }
 
 cudaError_t bs_apply_selected(chap_bs *h) { return launch_apply_gated(h->dev, h->plan, 0, h->st); }
+
+chap_status whole_instance_ok(chap_bs *h)
+{
+    if (h->shard_count > 1)
+        return fail(h, CHAP_E_STATE,
+                    "column-sharded handle: its pass covers a share of the columns; exchange the shards' move "
+                    "records (chap_bs_move_record) and apply the winner with chap_bs_apply_records");
+    return CHAP_OK;
+}
+
+chap_status own_scratch_ok(chap_bs *h)
+{
+    if (h->no_hist_scratch && h->info.n_hist_cols > 0)
+        return fail(h, CHAP_E_STATE,
+                    "handle created with static_scratch_only: its passes run through "
+                    "chap_bs_best_shift_static_scratch");
+    return CHAP_OK;
+}
 }  // namespace chap
 
 extern "C" {
@@ -271,10 +289,15 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     if (opts) h->opt = *opts; else chap_options_default(&h->opt);
     if (const char *f = std::getenv("CHAP_FAIL_ALLOC_AFTER")) h->fail_allocs_after = std::atol(f);
     if (!(h->opt.feas_tol >= 0.0) || h->opt.tenure < 0 || h->opt.graph_iters < 1 ||
-        (h->opt.lazy_binary != 0 && h->opt.lazy_binary != 1)) {
+        (h->opt.lazy_binary != 0 && h->opt.lazy_binary != 1) ||
+        (h->opt.static_scratch_only != 0 && h->opt.static_scratch_only != 1) ||
+        h->opt.shard_count < 0 || (h->opt.shard_count > 1 && (h->opt.shard_rank < 0 ||
+                                                              h->opt.shard_rank >= h->opt.shard_count))) {
         delete h;
         return CHAP_E_INVALID;
     }
+    h->shard_count = std::max(1, (int)h->opt.shard_count);
+    h->shard_rank = h->shard_count > 1 ? (int)h->opt.shard_rank : 0;
     h->st = static_cast<cudaStream_t>(stream);
     const int n = p->n, m = p->m;
     h->n = n;
@@ -347,17 +370,16 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         nb_bytes_vars += 16;
         const bool fin = std::isfinite(h->lb[j]) && std::isfinite(h->ub[j]);
         const double dom = fin ? h->ub[j] - h->lb[j] + 1 : INFINITY;
+        // sort entries: one per normalised half (a continuous variable's half
+        // may add a second, the marker of its tight point) and the bounds
+        const int per_half = t == CHAP_VAR_CONT ? 2 : 1;
         int64_t E = (std::isfinite(h->lb[j]) ? 1 : 0) + (std::isfinite(h->ub[j]) ? 1 : 0);
-        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += h->row_eq[p->row_idx[e]] ? 2 : 1;
+        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += (h->row_eq[p->row_idx[e]] ? 2 : 1) * per_half;
         int k;
         if (E <= kWarpSortMax) k = T_NB;
         else if (t == CHAP_VAR_INT && dom <= kHistMaxDomain) k = T_NB_HIST;
         else if (E <= kCtaMaxEntries) k = T_NB_CTA;
-        else {
-            std::fprintf(stderr, "chap_bs_create: column %d has %lld breakpoint entries and no on-chip path\n", j, (long long)E);
-            delete h;
-            return CHAP_E_UNSUPPORTED;
-        }
+        else k = T_NB_LONG;
         if (k == T_NB_CTA) cta_n.push_back(std::max(next_pow2((int)E), kCtaThreads));
         if (k == T_NB) nb_cap.push_back((int)E);
         kind_vars[k].push_back(j);
@@ -384,6 +406,29 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         nb_cap.swap(cs);
     }
     const int n_fixed = (int)fixed_vars.size();
+    // column shard (Sec. 3.1's pass split by columns over several GPUs): this
+    // handle evaluates every world-th column of each class (round robin over
+    // the class order, so every shard gets a like mix of lengths); the others
+    // stay in the store for the apply and sit, unevaluated, after the fixed
+    // variables
+    std::vector<int> other_vars;
+    if (h->shard_count > 1) {
+        auto keep = [&](std::vector<int> &v, std::vector<int> *aux) {
+            std::vector<int> kept, kept_aux;
+            for (size_t q = 0; q < v.size(); ++q) {
+                if ((int)(q % (size_t)h->shard_count) == h->shard_rank) {
+                    kept.push_back(v[q]);
+                    if (aux) kept_aux.push_back((*aux)[q]);
+                } else {
+                    other_vars.push_back(v[q]);
+                }
+            }
+            v.swap(kept);
+            if (aux) aux->swap(kept_aux);
+        };
+        for (int k = 0; k < T_NUM_KINDS; ++k)
+            keep(kind_vars[k], k == T_NB ? &nb_cap : (k == T_NB_CTA ? &cta_n : nullptr));
+    }
     std::vector<int> var_list;
     var_list.reserve(n);
     std::vector<int> kind_base(T_NUM_KINDS + 1, 0);
@@ -393,6 +438,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
     kind_base[T_NUM_KINDS] = (int)var_list.size();
     var_list.insert(var_list.end(), fixed_vars.begin(), fixed_vars.end());
+    var_list.insert(var_list.end(), other_vars.begin(), other_vars.end());
     std::vector<int> vpos(n);
     for (int q = 0; q < n; ++q) vpos[var_list[q]] = q;
 
@@ -433,8 +479,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     for (int k = T_NB; k < T_NUM_KINDS; ++k) {
         const int base = kind_base[k], cnt = kind_base[k + 1] - base;
         if (cnt == 0) continue;
-        if (k == T_NB) {
-            continue;  // one warp per column, no tiles
+        if (k == T_NB || k == T_NB_LONG) {
+            continue;  // one warp per column, no tiles; long lists: tiled below
         } else if (k == T_NB_CTA) {
             for (int b = 0; b < cnt; ++b) {
                 max_cta_n = std::max(max_cta_n, cta_n[b]);
@@ -458,6 +504,32 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
             }
         }
     }
+    // long lists: runs of kLongRun sorted entries per chunk of kLongChunk
+    // nonzeros, padded to a power of two runs per column
+    std::vector<LongCol> lcols;
+    std::vector<Tile> tiles_lgen, tiles_lscan;
+    long long long_entries = 0;
+    int long_rounds = 0, long_tiles = 0;
+    for (int q = kind_base[T_NB_LONG]; q < kind_base[T_NB_LONG + 1]; ++q) {
+        LongCol lc{};
+        lc.pos = q;
+        lc.e_mid = ci_ptr[q + 1] - ci_ptr[q];
+        lc.e_end = lc.e_mid + (cf_ptr[q + 1] - cf_ptr[q]);
+        lc.nchunks = std::max(1, (lc.e_end + kLongChunk - 1) / kLongChunk);
+        int runs = 1, rounds = 0;
+        while (runs < lc.nchunks) { runs <<= 1; ++rounds; }
+        lc.runs = runs;
+        long_rounds = std::max(long_rounds, rounds);
+        lc.ntiles = (int)((long long)runs * kLongRun / kLongTile);
+        lc.tile0 = long_tiles;
+        long_tiles += lc.ntiles;
+        lc.base = long_entries;
+        long_entries += (long long)runs * kLongRun;
+        const int li = (int)lcols.size();
+        for (int c = 0; c < runs; ++c) tiles_lgen.push_back(Tile{T_NB_LONG, li, li + 1, c});
+        for (int t2 = 0; t2 < lc.ntiles; ++t2) tiles_lscan.push_back(Tile{T_NB_LONG, li, li + 1, t2});
+        lcols.push_back(lc);
+    }
     const int nb_cols = kind_base[T_NB + 1] - kind_base[T_NB];
     // lanes per short non-binary column: 4 when the columns are short on average
     int nb_G = 8;
@@ -479,7 +551,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     const int n_tb = bin_cols > 0 ? bin_grid_size(bin_cols, bin_G) : 0, n_tc = (int)tiles_cta.size();
     const int slot_hist = n_tb + n_tn + n_tc;
     for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = slot_hist + (int)q;
-    const int n_bb = slot_hist + (int)hcols.size();
+    const int slot_long = slot_hist + (int)hcols.size();
+    for (size_t q = 0; q < lcols.size(); ++q) lcols[q].slot = slot_long + (int)q;
+    const int n_bb = slot_long + (int)lcols.size();
 
     // ---- device allocation
     Dev &d = h->dev;
@@ -520,9 +594,25 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     Tile *tc_d = dalloc<Tile>(h, tiles_cta.size());
     Tile *th_d = dalloc<Tile>(h, tiles_hist.size());
     HistCol *hc_d = dalloc<HistCol>(h, hcols.size());
-    d.hbins = dalloc<HBin>(h, hist_bins);
+    // the counting-sort scratch (none for a handle whose passes use the
+    // library's fixed scratch)
+    h->no_hist_scratch = h->opt.static_scratch_only != 0;
+    d.hbins = dalloc<HBin>(h, h->no_hist_scratch ? 0 : hist_bins);
     h->hist_bins = hist_bins;
-    d.hacc = dalloc<HistAcc>(h, hcols.size());
+    d.hacc = dalloc<HistAcc>(h, h->no_hist_scratch ? 0 : hcols.size());
+    const bool has_long = !lcols.empty();
+    if (has_long) {
+        d.lbuf0 = dalloc<SEntry>(h, (size_t)long_entries);
+        d.lbuf1 = dalloc<SEntry>(h, (size_t)long_entries);
+        d.lacc = dalloc<HistAcc>(h, lcols.size());
+        d.ltsum = dalloc<long long>(h, long_tiles);
+        d.ltsumc = dalloc<int>(h, long_tiles);
+        d.lcand = dalloc<LCand>(h, long_tiles);
+    }
+    LongCol *lc_d = dalloc<LongCol>(h, lcols.size());
+    Tile *tlg_d = dalloc<Tile>(h, tiles_lgen.size()), *tls_d = dalloc<Tile>(h, tiles_lscan.size());
+    d.n_long = (int)lcols.size();
+    h->t_rec = dalloc<chap_move_record>(h, kMaxRecords);
     h->t_xhat = dalloc<double>(h, n);
     h->t_s = dalloc<long long>(h, n);
     h->t_dc = dalloc<int>(h, n);
@@ -532,8 +622,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && ci_eq_d && cf_eq_d && row_ptr_d && col_idx_d &&
               row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.x_best && d.rs &&
               d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
-              d.hbins && d.hacc && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu &&
-              (!lazy || (d.lz_s && d.lz_dc && d.lz_mark && d.lz_list));
+              d.hbins && d.hacc && h->t_rec && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu &&
+              (!lazy || (d.lz_s && d.lz_dc && d.lz_mark && d.lz_list)) && lc_d && tlg_d && tls_d &&
+              (!has_long || (d.lbuf0 && d.lbuf1 && d.lacc && d.ltsum && d.ltsumc && d.lcand));
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
     if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
     for (int k = 0; k < 3 && ok; ++k)
@@ -556,6 +647,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     d.var_list = vl_d;
     d.vpos = vpos_d;
     d.hcols = hc_d;
+    d.lcols = lc_d;
     cudaStream_t st = h->st;
     std::vector<long long> rp(p->row_ptr, p->row_ptr + m + 1);
     cudaError_t e = cudaSuccess;
@@ -569,9 +661,14 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     UP(vl_d, var_list.data(), var_list.size()); UP(vpos_d, vpos.data(), n);
     UP(tc_d, tiles_cta.data(), tiles_cta.size());
     UP(th_d, tiles_hist.data(), tiles_hist.size()); UP(hc_d, hcols.data(), hcols.size());
+    UP(lc_d, lcols.data(), lcols.size());
+    UP(tlg_d, tiles_lgen.data(), tiles_lgen.size()); UP(tls_d, tiles_lscan.data(), tiles_lscan.size());
 #undef UP
-    if (e == cudaSuccess && hist_bins > 0) e = cudaMemsetAsync(d.hbins, 0, sizeof(HBin) * hist_bins, st);
-    if (e == cudaSuccess && !hcols.empty()) e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
+    if (e == cudaSuccess && has_long) e = cudaMemsetAsync(d.lacc, 0, sizeof(HistAcc) * lcols.size(), st);
+    if (e == cudaSuccess && hist_bins > 0 && !h->no_hist_scratch)
+        e = cudaMemsetAsync(d.hbins, 0, sizeof(HBin) * hist_bins, st);
+    if (e == cudaSuccess && !hcols.empty() && !h->no_hist_scratch)
+        e = cudaMemsetAsync(d.hacc, 0, sizeof(HistAcc) * hcols.size(), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess && lazy) e = cudaMemsetAsync(d.lz_mark, 0, sizeof(unsigned) * bin_cols, st);
     if (e == cudaSuccess && lazy) e = launch_lazy_init(d, st);
@@ -583,6 +680,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
     pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);
     pl.slot_nb = n_tb; pl.slot_cta = n_tb + n_tn;
+    pl.tiles_lgen = tlg_d; pl.n_lgen = (int)tiles_lgen.size();
+    pl.tiles_lscan = tls_d; pl.n_lscan = (int)tiles_lscan.size();
+    pl.long_rounds = long_rounds; pl.long_entries = long_entries;
     if (e == cudaSuccess) e = setup_kernel_attributes(pl);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -598,15 +698,17 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     in.n = n; in.m = m; in.m_norm = mn;
     in.n_bin = n_bin; in.n_int = n_int; in.n_cont = n_cont; in.n_fixed = n_fixed;
     in.nnz = p->nnz; in.nnz_int_rows = nnz_int; in.nnz_fp_rows = p->nnz - nnz_int;
-    in.eval_blocks = n_tb + n_tn + n_tc + (int)tiles_hist.size();
+    in.eval_blocks = n_tb + n_tn + n_tc + (int)tiles_hist.size() + (int)tiles_lscan.size();
     in.n_hist_cols = (int)hcols.size();
+    in.n_long_cols = (int)lcols.size();
     // evaluation kernels (they also select the move), a selection kernel only
     // when none runs, the move apply and the weight bump
     in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + (n_bb == 0) + 2 +
-                           (lazy ? 2 : 0);   // kept binary scores: the scan and the marking kernel
+                           (lazy ? 2 : 0) +   // kept binary scores: the scan and the marking kernel
+                           (has_long ? 3 + long_rounds : 0);   // long lists: generation, merges, tile sums, scan
     // algorithmic bytes of one pass: every nonzero once (row + coefficient),
     // every row state and tolerance once, every active variable's state once.
-    int64_t n_act = n - n_fixed;
+    int64_t n_act = kind_base[T_NUM_KINDS];   // evaluated columns
     in.bytes_per_pass = 8 * nnz_int + 12 * (p->nnz - nnz_int) + 16LL * (m - m_fp) + 32LL * m_fp +
                         n_act * (8 /*x*/ + 8 /*column pointers*/ + 8 /*tabu*/ + 1 /*type*/) + nb_bytes_vars;
     // algorithmic bytes of one launch of the binary and short-column kernels:
@@ -669,7 +771,8 @@ chap_status chap_bs_kernel_ms(chap_bs *h, float *ms)
     if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
     if (!h->prof_valid) return fail(h, CHAP_E_STATE, "no profiled pass since chap_bs_profile(h, 1)");
     CK(h, cudaStreamSynchronize(h->st), "synchronise");
-    const bool launched[5] = {h->plan.n_bin > 0, h->plan.nb_grid > 0, h->plan.n_cta > 0, h->plan.n_hist_tiles > 0, true};
+    const bool launched[5] = {h->plan.n_bin > 0, h->plan.nb_grid > 0, h->plan.n_cta > 0 || h->plan.n_lgen > 0,
+                              h->plan.n_hist_tiles > 0, true};
     for (int k = 0; k < 5; ++k) {
         ms[k] = 0.0f;
         if (launched[k]) CK(h, cudaEventElapsedTime(&ms[k], h->plan.pev[2 * k], h->plan.pev[2 * k + 1]), "kernel timing");
@@ -768,6 +871,7 @@ chap_status chap_bs_best_shift(chap_bs *h, double *xhat, int64_t *score_half, in
     if (!h) return CHAP_E_INVALID;
     if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
     if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    if (own_scratch_ok(h) != CHAP_OK) return CHAP_E_STATE;
     VarOut o{nullptr, nullptr, nullptr};
     bool host = mem == CHAP_MEM_HOST;
     if (xhat) o.xhat = host ? h->t_xhat : xhat;
@@ -816,6 +920,7 @@ chap_status chap_bs_best_shift_static_scratch(chap_bs *h, double *xhat, int64_t 
     if (dnviol) o.dc = host ? h->t_dc : dnviol;
     CK(h, launch_eval_gated(d, h->plan, o, 0, h->st), "best-shift kernels");
     CK(h, launch_select_gated(d, h->plan, 0, h->st), "selection kernel");
+    if (h->plan.profile) h->prof_valid = true;
     if (host && h->n) {
         if (xhat) CK(h, cudaMemcpyAsync(xhat, h->t_xhat, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st), "copy xhat");
         if (score_half) CK(h, cudaMemcpyAsync(score_half, h->t_s, sizeof(long long) * h->n, cudaMemcpyDeviceToHost, h->st), "copy scores");
@@ -851,10 +956,48 @@ chap_status chap_bs_apply(chap_bs *h, int32_t var, double new_value)
     return CHAP_OK;
 }
 
+chap_status chap_bs_move_record(chap_bs *h, chap_move_record *rec, int32_t mem)
+{
+    if (!h || !rec) return h ? fail(h, CHAP_E_INVALID, "NULL record") : CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    if (mem == CHAP_MEM_DEVICE) {
+        CK(h, launch_move_record(h->dev, rec, h->st), "move record");
+        return CHAP_OK;
+    }
+    CK(h, launch_move_record(h->dev, h->t_rec, h->st), "move record");
+    CK(h, cudaMemcpyAsync(rec, h->t_rec, sizeof(chap_move_record), cudaMemcpyDeviceToHost, h->st), "copy record");
+    CK(h, cudaStreamSynchronize(h->st), "synchronise");
+    return CHAP_OK;
+}
+
+chap_status chap_bs_apply_records(chap_bs *h, const chap_move_record *recs, int32_t k, int32_t mem)
+{
+    if (!h || !recs) return h ? fail(h, CHAP_E_INVALID, "NULL records") : CHAP_E_INVALID;
+    if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
+    if (k < 1 || k > kMaxRecords) return fail(h, CHAP_E_INVALID, "record count out of range [1, 1024]");
+    const chap_move_record *src = recs;
+    if (mem == CHAP_MEM_HOST) {
+        for (int q = 0; q < k; ++q) {
+            const chap_move_record &r = recs[q];
+            if (r.score_half > 0 && (r.var < 0 || r.var >= h->n))
+                return fail(h, CHAP_E_INVALID, "record names a variable out of range");
+        }
+        CK(h, cudaMemcpyAsync(h->t_rec, recs, sizeof(chap_move_record) * k, cudaMemcpyHostToDevice, h->st),
+           "copy records");
+        src = h->t_rec;
+    }
+    CK(h, launch_apply_records(h->dev, src, k, h->st), "select record");
+    CK(h, launch_apply_gated(h->dev, h->plan, 0, h->st), "apply kernel");
+    return CHAP_OK;
+}
+
 chap_status chap_bs_step(chap_bs *h, chap_move *out)
 {
     if (!h) return CHAP_E_INVALID;
     if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (own_scratch_ok(h) != CHAP_OK || whole_instance_ok(h) != CHAP_OK) return CHAP_E_STATE;
     VarOut o{nullptr, nullptr, nullptr};
     CK(h, launch_eval_gated(h->dev, h->plan, o, 0, h->st), "best-shift kernels");
     CK(h, launch_select_gated(h->dev, h->plan, 0, h->st), "selection kernel");
@@ -918,6 +1061,7 @@ chap_status chap_tabu_run(chap_bs *h, const chap_options *opts, chap_tabu_result
 {
     if (!h || !res) return h ? fail(h, CHAP_E_INVALID, "NULL result") : CHAP_E_INVALID;
     if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (own_scratch_ok(h) != CHAP_OK || whole_instance_ok(h) != CHAP_OK) return CHAP_E_STATE;
     chap_options o = opts ? *opts : h->opt;
     if (o.graph_iters < 1 || o.max_iters < 0) return fail(h, CHAP_E_INVALID, "bad run options");
     if (o.tenure != h->opt.tenure) return fail(h, CHAP_E_INVALID, "tenure is fixed at create time");
@@ -965,13 +1109,13 @@ chap_status chap_tabu_run(chap_bs *h, const chap_options *opts, chap_tabu_result
     res->best_nviol = c.best_nviol;
     res->seconds = std::chrono::duration<double>(t1 - t0).count();
     res->time_to_feasible_s = c.feasible_iter >= 0 ? (double)(c.t_feas_ns - c.t_start_ns) * 1e-9 : -1.0;
-    std::vector<double> x(h->n);
+    // c^T x reduced on the device; only the value crosses to the host
+    double obj = 0.0;
     if (h->n) {
-        CK(h, cudaMemcpyAsync(x.data(), d.x, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st), "copy x");
+        CK(h, launch_objective(d, h->t_xhat, h->st), "objective");
+        CK(h, cudaMemcpyAsync(&obj, h->t_xhat, sizeof(double), cudaMemcpyDeviceToHost, h->st), "copy objective");
         CK(h, cudaStreamSynchronize(h->st), "synchronise");
     }
-    double obj = 0.0;
-    for (int j = 0; j < h->n; ++j) obj += h->obj[j] * x[j];
     res->objective = obj;
     return CHAP_OK;
 }

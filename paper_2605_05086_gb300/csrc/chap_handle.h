@@ -35,7 +35,10 @@ struct chap_bs {
     int g_iters = 0;
     bool broken = false;
     bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
+    chap_move_record *t_rec = nullptr;  // move records staged from host memory
+    int shard_rank = 0, shard_count = 1;  // column shard evaluated by this handle
     int64_t hist_bins = 0;     // counting-sort bins of the instance
+    bool no_hist_scratch = false; // created without the counting-sort scratch (static_scratch_only)
     long fail_allocs_after = -1; // device allocations left before an injected failure (-1: none)
     void *learn = nullptr;     // state of the learned driver (learned.cu), created on first use
     std::string err;
@@ -46,5 +49,13 @@ namespace chap {
 // with optional device per-variable outputs; the apply of the selected move.
 cudaError_t bs_pass(chap_bs *h, const VarOut &o);
 cudaError_t bs_apply_selected(chap_bs *h);
+// CHAP_OK when the handle may run a pass on its own scratch; CHAP_E_STATE (with
+// the handle's message set) when it was created without the counting-sort
+// scratch and the instance has counting-sorted columns.
+chap_status own_scratch_ok(chap_bs *h);
+// CHAP_OK unless the handle evaluates only a column shard (then a pass gives
+// the shard's best move, not the instance's: CHAP_E_STATE with a message).
+chap_status whole_instance_ok(chap_bs *h);
+constexpr int kMaxRecords = 1024;   // move records one chap_bs_apply_records call reduces
 void learn_free(chap_bs *h);   // releases h->learn (learned.cu)
 }  // namespace chap

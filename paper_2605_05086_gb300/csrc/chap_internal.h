@@ -30,6 +30,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/chap.h"
+
 namespace chap {
 
 constexpr int kVarBin = 0, kVarInt = 1, kVarCont = 2;
@@ -113,6 +115,7 @@ enum TileKind : int {
     T_NB,                     // short breakpoint lists: one warp per column
     T_NB_CTA,                 // CTA bitonic sort in shared memory
     T_NB_HIST,                // multi-CTA counting sort (long integer columns)
+    T_NB_LONG,                // multi-CTA merge sort (lists longer than a CTA sorts)
     T_NUM_KINDS
 };
 
@@ -149,6 +152,39 @@ struct __align__(16) HistAcc {
     int beta_c, alpha_c;
     unsigned int ticket;
     int pad;
+};
+
+// Breakpoint entry staged in shared memory (and in the long lists' global
+// buffers): key (t in order-preserving form), score delta (|delta| <= 2w <
+// 2^31), aux = entry class and count delta.
+struct __align__(16) SEntry {
+    unsigned long long key;
+    int del;
+    unsigned aux;
+};
+
+// Best candidate of one scan tile of a long list (score, key, count change).
+struct __align__(8) LCand {
+    long long s;
+    unsigned long long key;
+    int dc;
+    int valid;
+};
+
+// A column whose breakpoint list is longer than one CTA sorts (continuous
+// variables, integer variables with a wide domain): its entries are generated
+// and sorted in runs of kLongRun entries, one chunk of kLongChunk nonzeros per
+// CTA, the runs merged pairwise across the grid, and the merged list scanned
+// in tiles of kLongTile entries with a carry across tiles.
+struct LongCol {
+    int pos;              // position of the column in var_list
+    int nchunks;          // chunks of kLongChunk nonzeros (= generated runs)
+    int runs;             // runs rounded up to a power of two (pads: empty runs)
+    int e_mid, e_end;     // virtual entry range: [0, e_mid) integral part, [e_mid, e_end) FP part
+    int ntiles;           // scan tiles of the merged list
+    int tile0;            // first tile of the column in the per-tile arrays
+    int slot;             // block_best slot of the column
+    long long base;       // first entry of the column in the entry buffers
 };
 
 struct Dev {
@@ -194,15 +230,19 @@ struct Dev {
     HBin *hbins;
     HistAcc *hacc;
     const HistCol *hcols;
+    // long lists: entry buffers (ping-pong of the merge), per-column
+    // accumulators, per-tile sums and candidates, column table
+    SEntry *lbuf0, *lbuf1;
+    HistAcc *lacc;
+    long long *ltsum;        // per tile: score delta sum
+    int *ltsumc;             // per tile: count delta sum
+    LCand *lcand;            // per tile: best candidate
+    const LongCol *lcols;
+    int n_long;
+    int pad2;
 };
 
-// Breakpoint entry staged in shared memory: key (t in order-preserving form),
-// score delta (|delta| <= 2w < 2^31), aux = post marker and count delta.
-struct __align__(16) SEntry {
-    unsigned long long key;
-    int del;
-    unsigned aux;
-};
+
 
 // Optional per-variable outputs of a best-shift pass (device pointers, may be null).
 struct VarOut {
@@ -224,6 +264,12 @@ struct LaunchPlan {
     const Tile *tiles_hist;
     int n_hist_tiles;
     int hist_smem;
+    const Tile *tiles_lgen;    // long lists: (column, chunk) of the generation kernel
+    int n_lgen;
+    const Tile *tiles_lscan;   // (column, tile) of the scan kernels
+    int n_lscan;
+    int long_rounds;           // pairwise merge rounds (log2 of the most runs)
+    long long long_entries;    // entries of all long lists (merge grid)
     int slot_nb, slot_cta;     // first block_best slot of each kernel
     int lazy;                  // binary flips through the kept scores (k_eval_bin_lazy, k_bin_scan)
     int lazy_mark_blocks;      // CTAs of the marking kernel
@@ -241,6 +287,7 @@ struct LaunchPlan {
 // Kernel launchers (kernels.cu).  All are asynchronous on `st`; `gate` makes a
 // kernel return at once when the run's done flag is set (graph replays).
 cudaError_t setup_kernel_attributes(const LaunchPlan &p);
+int long_gen_smem();                  // dynamic shared memory of the long lists' generation kernel
 // Device addresses of the fixed counting-sort scratch (kStaticHistBins bins,
 // kStaticHistCols accumulators) on the current device.
 cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc);
@@ -259,6 +306,9 @@ cudaError_t launch_lazy_init(const Dev &d, cudaStream_t st);
 cudaError_t launch_unpack_w(const Dev &d, int *w_norm, cudaStream_t st);
 cudaError_t launch_unpack_r(const Dev &d, double *r_norm, cudaStream_t st);
 cudaError_t launch_tabu_convert(int n, const int *src32, long long *dst64, cudaStream_t st);
+cudaError_t launch_objective(const Dev &d, double *out, cudaStream_t st);  // c^T x into out[0] (device)
+cudaError_t launch_move_record(const Dev &d, chap_move_record *rec, cudaStream_t st);
+cudaError_t launch_apply_records(const Dev &d, const chap_move_record *recs, int k, cudaStream_t st);
 
 // Sizes used by both sides.
 constexpr int kEvalThreads = 256;
@@ -267,6 +317,10 @@ constexpr int kCtaThreads = 512;
 constexpr int kHistMaxDomain = 4096;    // largest integer domain of the multi-CTA counting sort
 constexpr int kHistChunk = 16384;       // matrix entries per counting-sort CTA
 constexpr int kHistThreads = 512;
+constexpr int kLongChunk = 1020;       // nonzeros per generating CTA: <= 4 entries each, + 2 bounds
+constexpr int kLongRun = 4096;         // entries of one sorted run (power of two)
+constexpr int kLongThreads = 512;
+constexpr int kLongTile = 2048;        // entries per scan CTA (4 per thread)
 constexpr int kStaticHistBins = 1 << 16;  // fixed counting-sort scratch: bins (24 B each, 1.5 MiB)
 constexpr int kStaticHistCols = 256;      // and columns
 constexpr int kApplyThreads = 256;

@@ -37,9 +37,11 @@
 // order-preserving integer keys.  Scores are int64 half-weight counts.
 #include "chap_internal.h"
 
+#include <algorithm>
 #include <climits>
-#include <type_traits>
 #include <cstdint>
+#include <mutex>
+#include <type_traits>
 
 namespace chap {
 
@@ -724,11 +726,18 @@ struct Acc {
 
 // Entry of one normalised half: type 1 "pre" (a < 0: delta D counts from t on,
 // violation count -1), type 2 "post" (a > 0: t is a candidate, D counts right of
-// t, violation count +1), type 0 none.
+// t, violation count +1), type 0 none.  On a continuous variable the delta
+// entry sits where the row's status changes (the boundary of its satisfied set
+// within eps) and is not a candidate itself (nocand); the candidate is the
+// point where the row becomes tight, a separate marker entry (mark, mkey) with
+// no delta.
 struct Half {
     unsigned long long key;
     long long D;
     int type;
+    int nocand;
+    int mark;
+    unsigned long long mkey;
 };
 
 // Case table of Algorithm 1 for one normalised half (half-weight units).  The
@@ -738,6 +747,8 @@ __device__ __forceinline__ void half_case(bool viol, bool tight, bool apos, int 
                                           long long w, unsigned long long kl, unsigned long long ku, Acc &acc, Half &h)
 {
     h.type = 0;
+    h.nocand = 0;
+    h.mark = 0;
     if (tight) {
         if (apos) { acc.alpha -= 2 * w; acc.alpha_c += 1; }
         else { acc.beta -= 2 * w; acc.alpha += 2 * w; acc.beta_c += 1; acc.alpha_c -= 1; }
@@ -812,31 +823,68 @@ __device__ __forceinline__ int int_fp_side(double m, double a, bool apos, const 
     return 0;
 }
 
-// Continuous variable: side of t = xbar - r / a (t < l <=> r/a > xbar - l,
-// t > u <=> r/a < xbar - u), decided from single-precision products with a
-// margin that also covers the rounding of t itself; else 0.
-__device__ __forceinline__ int cont_fp_side(double r, double a, bool apos, const ColCtx &c)
+// Continuous variable: side of xbar - q / a (left of l <=> q/a > xbar - l,
+// right of u <=> q/a < xbar - u) for q = r (the tight point) or q = -m (the
+// boundary), decided from single-precision products with a margin that also
+// covers the rounding of the point itself; else 0.
+__device__ __forceinline__ int cont_side1(float qf, float af, bool apos, const ColCtx &c)
 {
-    bool ok = c.fok;
-    const float rf = approx_f(r, ok), af = approx_f(a, ok);
-    if (!ok) return 0;
     const float tol = c.xaf * fabsf(af) * 1.0e-10f;
     const float P = c.dlf * af, Q = c.duf * af;
     if (apos) {
-        if (rf - slack(rf) - tol > P + slack(P)) return -1;
-        if (rf + slack(rf) + tol < Q - slack(Q)) return 1;
+        if (qf - slack(qf) - tol > P + slack(P)) return -1;
+        if (qf + slack(qf) + tol < Q - slack(Q)) return 1;
     } else {
-        if (rf + slack(rf) + tol < P - slack(P)) return -1;
-        if (rf - slack(rf) - tol > Q + slack(Q)) return 1;
+        if (qf + slack(qf) + tol < P - slack(P)) return -1;
+        if (qf - slack(qf) - tol > Q + slack(Q)) return 1;
     }
     return 0;
+}
+
+// Both points of a continuous half (tight point t = xbar - r/a and boundary
+// tb = xbar + m/a) certainly left of l (-1) or right of u (+1); else 0.
+__device__ __forceinline__ int cont_fp_side(double r, double m, double a, bool apos, const ColCtx &c)
+{
+    bool ok = c.fok;
+    const float rf = approx_f(r, ok), mf = approx_f(m, ok), af = approx_f(a, ok);
+    if (!ok) return 0;
+    const int s1 = cont_side1(rf, af, apos, c);
+    return s1 != 0 && cont_side1(-mf, af, apos, c) == s1 ? s1 : 0;
+}
+
+__device__ __forceinline__ unsigned long long cont_key(double t)
+{
+    const unsigned long long k = dkey(t);
+    return k == dkey(-0.0) ? dkey(0.0) : k;
+}
+
+// Continuous variable, one normalised half with residual r, coefficient a and
+// margin m = eps - r (Algorithm 1 with the tolerance of the definition): the
+// row is satisfied at x iff a (x - xbar) <= m, i.e. up to (a > 0) or from
+// (a < 0) the boundary tb = xbar + m / a, so the delta of the case table sits
+// at tb (not a candidate itself).  The candidate of the row is its tight point
+// t = xbar - r / a, a marker entry, unless |r| <= eps (near0): such a row is
+// already tight and its point is xbar.
+__device__ __forceinline__ void cont_exact(double r, double a, double m, bool viol, bool near0, long long w,
+                                           const ColCtx &c, Acc &acc, Half &h)
+{
+    const bool apos = !dneg(a);
+    half_case(viol, false, apos, 0, cont_key(__dadd_rn(c.xb, __ddiv_rn(m, a))), w, c.kl, c.ku, acc, h);
+    h.nocand = 1;
+    if (!near0) {
+        const unsigned long long k = cont_key(__dsub_rn(c.xb, __ddiv_rn(r, a)));
+        if (k != c.kxb && k >= c.kl && k <= c.ku) {
+            h.mark = 1;
+            h.mkey = k;
+        }
+    }
 }
 
 // Non-integral row, one half with residual r, coefficient a and margins
 // m = eps - r (own), mo = eps + r (other half).  Integer variable: the last
 // integer at which the row is satisfied within eps.  Continuous variable:
-// t = xbar - r / a (the row becomes tight); tight when |r| <= eps or t == xbar.
-// The double division runs only when the side test cannot place t outside [l, u].
+// cont_exact.  The double divisions run only when the side test cannot place
+// the half's points outside [l, u].
 __device__ __forceinline__ void fp_half(double r, double a, double m, double mo, long long w, const ColCtx &c,
                                         Acc &acc, Half &h)
 {
@@ -853,23 +901,20 @@ __device__ __forceinline__ void fp_half(double r, double a, double m, double mo,
         half_case(viol, !viol && dd == 0, apos, 0, ikey(c.xbi + dd), w, c.kl, c.ku, acc, h);
     } else {
         const bool near0 = !viol && !dneg(mo);  // |r| <= eps
-        const int side = cont_fp_side(r, a, apos, c);
+        const int side = cont_fp_side(r, m, a, apos, c);
         if (side != 0) {
-            half_case(viol, near0, apos, side, 0ull, w, c.kl, c.ku, acc, h);
+            half_case(viol, false, apos, side, 0ull, w, c.kl, c.ku, acc, h);
             return;
         }
-        const double t = __dsub_rn(c.xb, __ddiv_rn(r, a));
-        unsigned long long k = dkey(t);
-        if (k == dkey(-0.0)) k = dkey(0.0);
-        half_case(viol, near0 || (!viol && k == c.kxb), apos, 0, k, w, c.kl, c.ku, acc, h);
+        cont_exact(r, a, m, viol, near0, w, c, acc, h);
     }
 }
 
 // Both halves of the v-th nonzero of the column (integral part first).
 __device__ __forceinline__ void gen_entry(const Dev &d, const ColCtx &c, int v, Acc &acc, Half &h1, Half &h2)
 {
-    h1.type = 0;
-    h2.type = 0;
+    h1.type = 0; h1.mark = 0;
+    h2.type = 0; h2.mark = 0;
     if (v < c.nI) {
         const int e = c.ci0 + v;
         const int i = __ldg(d.ci_row + e);
@@ -901,32 +946,60 @@ __device__ __forceinline__ void warp_allreduce_acc(Acc &a)
     }
 }
 
-// aux word of a sort entry: bit 31 = post marker, bits 0..1 = count delta + 1.
-__device__ __forceinline__ unsigned make_aux(int post, int dc) { return ((unsigned)post << 31) | (unsigned)(dc + 1); }
+// aux word of a sort entry: bits 31..30 = class, bits 0..1 = count delta + 1.
+// Classes in their order at equal t: 0 pre entry that is no candidate (the
+// boundary delta of a continuous half), 1 pre entry (also bounds and the
+// tight-point markers, delta 0), 2 post entry, 3 post entry that is no
+// candidate.  Bit 31 is the post marker of Algorithm 1's (t, marker) order.
+constexpr int kClsPreDelta = 0, kClsPre = 1, kClsPost = 2, kClsPostDelta = 3;
+__device__ __forceinline__ unsigned make_aux(int cls, int dc) { return ((unsigned)cls << 30) | (unsigned)(dc + 1); }
 __device__ __forceinline__ int aux_dc(unsigned a) { return (int)(a & 3u) - 1; }
 __device__ __forceinline__ unsigned aux_post(unsigned a) { return a >> 31; }
+__device__ __forceinline__ unsigned aux_cls(unsigned a) { return a >> 30; }
+
+// Sort entry of a half's delta and of its marker.
+__device__ __forceinline__ unsigned half_aux(const Half &h)
+{
+    return h.type == 1 ? make_aux(h.nocand ? kClsPreDelta : kClsPre, -1) : make_aux(h.nocand ? kClsPostDelta : kClsPost, 1);
+}
+__device__ __forceinline__ unsigned marker_aux() { return make_aux(kClsPre, 0); }
+
+// Number of sort entries of a half (delta and marker).
+__device__ __forceinline__ int half_entries(const Half &h) { return (h.type != 0) + h.mark; }
 
 __device__ __forceinline__ void put_half(const Half &h, int pos, unsigned long long *k, long long *dl, unsigned *ax)
 {
-    k[pos] = h.key;
-    dl[pos] = h.D;
-    ax[pos] = h.type == 1 ? make_aux(0, -1) : make_aux(1, 1);
+    if (h.type != 0) {
+        k[pos] = h.key;
+        dl[pos] = h.D;
+        ax[pos] = half_aux(h);
+        ++pos;
+    }
+    if (h.mark) {
+        k[pos] = h.mkey;
+        dl[pos] = 0;
+        ax[pos] = marker_aux();
+    }
 }
 
-// Lexicographic (t, marker) order: pre entries before post entries at equal t.
+// Lexicographic (t, class) order: pre entries before post entries at equal t.
 __device__ __forceinline__ bool entry_less(unsigned long long k1, unsigned a1, unsigned long long k2, unsigned a2)
 {
-    return k1 < k2 || (k1 == k2 && aux_post(a1) < aux_post(a2));
+    return k1 < k2 || (k1 == k2 && aux_cls(a1) < aux_cls(a2));
 }
 
 // Candidate test of a sorted entry given its neighbours (Algorithm 1, phase 4):
-// the last pre entry of an equal-t run, or a post entry that opens its run.
-__device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, unsigned long long kprev, bool has_prev,
-                                             unsigned long long knext, unsigned anext)
+// the last class-1 entry of an equal-t run (every pre delta at t counted), or
+// the first post entry of a run without class-1 entries (no post delta at t
+// counted).  Boundary deltas are never candidates.
+__device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, unsigned long long kprev, unsigned aprev,
+                                             bool has_prev, unsigned long long knext, unsigned anext)
 {
     if (k == kPadKey) return false;
-    if (aux_post(a) == 0) return knext != k || aux_post(anext) != 0;
-    return !has_prev || kprev != k;
+    const unsigned c = aux_cls(a);
+    if (c == kClsPre) return knext != k || aux_cls(anext) != kClsPre;
+    if (c == kClsPost) return !has_prev || kprev != k || aux_cls(aprev) == kClsPreDelta;
+    return false;
 }
 
 // ------------------------------------------------- short non-binary columns
@@ -970,10 +1043,10 @@ struct NbGeom {
 // Undecided half (operands already negated for the second half of an "=" row):
 //  integral row:      x = r, a (int64);
 //  non-integral row:  x = eps - r (integer variable) or r (continuous), a (double bits),
-// meta = group | row kind << 3 | violated << 4.  A queued half of a continuous
-// variable is never "near 0" (|r| <= eps): those are decided by the pre-filter.
-struct __align__(8) QItem {
-    long long x, a;
+//                     y = eps - r (continuous);
+// meta = group | row kind << 3 | violated << 4 | near 0 (|r| <= eps) << 5.
+struct __align__(16) QItem {
+    long long x, a, y;
     int w, meta;
 };
 
@@ -1008,16 +1081,16 @@ __device__ __forceinline__ void acc_decided(int idx, int w, Acc &acc)
     acc.alpha_c += (int)((kTabAC >> (2 * idx)) & 3u) - 1;
 }
 
-// Side of a breakpoint from single-precision products (z / a against the
-// thresholds L, U of the column, a > 0 after normalisation), with relative
-// margins covering the float estimates and an absolute term tol: sets left /
-// right only when certain.
-__device__ __forceinline__ void side_test(float z, float a, float L, float U, float tol, bool &left, bool &right)
+// Side of the points z / a for z in [zlo, zhi] from single-precision products
+// (against the thresholds L, U of the column, a > 0 after normalisation), with
+// relative margins covering the float estimates and an absolute term tol: sets
+// left / right only when certain for both ends.
+__device__ __forceinline__ void side_test(float zlo, float zhi, float a, float L, float U, float tol, bool &left,
+                                          bool &right)
 {
     const float P = L * a, Q = U * a;
-    const float az = fabsf(z) * 1.0e-5f + tol + 1.0e-30f;
-    left = z + az < P - (fabsf(P) * 1.0e-5f + 1.0e-30f);
-    right = z - az > Q + (fabsf(Q) * 1.0e-5f + 1.0e-30f);
+    left = zhi + (fabsf(zhi) * 1.0e-5f + tol + 1.0e-30f) < P - (fabsf(P) * 1.0e-5f + 1.0e-30f);
+    right = zlo - (fabsf(zlo) * 1.0e-5f + tol + 1.0e-30f) > Q + (fabsf(Q) * 1.0e-5f + 1.0e-30f);
 }
 
 // Exact breakpoint of one queued half (Algorithm 1 case table, as int_half /
@@ -1042,10 +1115,9 @@ __device__ __forceinline__ void exact_item(const QItem &it, const ColCtx &ci, Ac
             tight = !viol && dd == 0;
             key = ikey(ci.xbi + dd);
         } else {
-            const double t = __dsub_rn(ci.xb, __ddiv_rn(__longlong_as_double(it.x), a));
-            key = dkey(t);
-            if (key == dkey(-0.0)) key = dkey(0.0);
-            tight = !viol && key == ci.kxb;
+            cont_exact(__longlong_as_double(it.x), a, __longlong_as_double(it.y), viol, ((it.meta >> 5) & 1) != 0, it.w,
+                       ci, acc, h);
+            return;
         }
     }
     half_case(viol, tight, apos, 0, key, it.w, ci.kl, ci.ku, acc, h);
@@ -1063,16 +1135,21 @@ __device__ __noinline__ void flush_queue(NbWarp<G> &W, int head, int n, int lane
         Acc acc{0, 0, 0, 0};
         Half h;
         h.type = 0;
+        h.mark = 0;
         exact_item(it, W.ctx[g], acc, h);
         if (acc.beta) atomicAdd(reinterpret_cast<unsigned long long *>(&W.beta[g]), (unsigned long long)acc.beta);
         if (acc.alpha) atomicAdd(reinterpret_cast<unsigned long long *>(&W.alpha[g]), (unsigned long long)acc.alpha);
         if (acc.beta_c) atomicAdd(&W.beta_c[g], acc.beta_c);
         if (acc.alpha_c) atomicAdd(&W.alpha_c[g], acc.alpha_c);
-        if (h.type != 0) {
-            const int pos = atomicAdd(&W.cnt[g], 1);
-            if (pos < NbGeom<G>::kStage)
-                W.stage[g * NbGeom<G>::kStage + pos] =
-                    SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
+        const int ne = half_entries(h);
+        if (ne) {
+            int pos = atomicAdd(&W.cnt[g], ne);
+            SEnt *st = W.stage + g * NbGeom<G>::kStage;
+            if (h.type != 0) {
+                if (pos < NbGeom<G>::kStage) st[pos] = SEnt{h.key, (int)h.D, half_aux(h)};
+                ++pos;
+            }
+            if (h.mark && pos < NbGeom<G>::kStage) st[pos] = SEnt{h.mkey, 0, marker_aux()};
         }
     }
     __syncwarp();
@@ -1081,10 +1158,10 @@ __device__ __noinline__ void flush_queue(NbWarp<G> &W, int head, int n, int lane
 // Candidate evaluation of one sorted entry (prefix sums P / Pc inclusive).
 __device__ __forceinline__ void eval_entry(VCand &vb, const ColCtx &c, const Acc &a, unsigned long long kk,
                                            long long del, unsigned aux, long long P, int Pc, unsigned long long kprev,
-                                           bool has_prev, unsigned long long knext, unsigned anext, long long nviol,
-                                           long long bestnv)
+                                           unsigned aprev, bool has_prev, unsigned long long knext, unsigned anext,
+                                           long long nviol, long long bestnv)
 {
-    if (!is_candidate(kk, aux, kprev, has_prev, knext, anext)) return;
+    if (!is_candidate(kk, aux, kprev, aprev, has_prev, knext, anext)) return;
     const bool post = aux_post(aux) != 0;
     const long long Pi = P - (post ? del : 0);
     const int Pci = Pc - (post ? aux_dc(aux) : 0);
@@ -1158,7 +1235,7 @@ __device__ __forceinline__ VCand group_sort_scan(const ColCtx &c, const Acc &a, 
     for (int k = 0; k < K; ++k) {
         const int idx = sub * K + k;
         if (idx < cnt) load_entry(list + idx, key[k], del[k], aux[k]);
-        else { key[k] = kPadKey; del[k] = 0; aux[k] = make_aux(1, 0); }
+        else { key[k] = kPadKey; del[k] = 0; aux[k] = make_aux(kClsPost, 0); }
     }
     group_bitonic<K, G>(key, del, aux, sub);
     long long P[K];
@@ -1180,15 +1257,17 @@ __device__ __forceinline__ VCand group_sort_scan(const ColCtx &c, const Acc &a, 
     unsigned long long nk = __shfl_down_sync(FULLMASK, key[0], 1, G);
     unsigned na = __shfl_down_sync(FULLMASK, aux[0], 1, G);
     const unsigned long long pk = __shfl_up_sync(FULLMASK, key[K - 1], 1, G);
-    if (sub == G - 1) { nk = kPadKey; na = make_aux(1, 0); }
+    const unsigned pa = __shfl_up_sync(FULLMASK, aux[K - 1], 1, G);
+    if (sub == G - 1) { nk = kPadKey; na = make_aux(kClsPost, 0); }
     VCand vb{0, 0ull, 0, 0};
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const unsigned long long knext = (k + 1 < K) ? key[(k + 1) % K] : nk;
         const unsigned anext = (k + 1 < K) ? aux[(k + 1) % K] : na;
         const unsigned long long kprev = (k > 0) ? key[(k + K - 1) % K] : pk;
-        eval_entry(vb, c, a, key[k], del[k], aux[k], ex + P[k], exc + Pc[k], kprev, k > 0 || sub > 0, knext, anext,
-                   nviol, bestnv);
+        const unsigned aprev = (k > 0) ? aux[(k + K - 1) % K] : pa;
+        eval_entry(vb, c, a, key[k], del[k], aux[k], ex + P[k], exc + Pc[k], kprev, aprev, k > 0 || sub > 0, knext,
+                   anext, nviol, bestnv);
     }
 #pragma unroll
     for (int o = G >> 1; o > 0; o >>= 1) {
@@ -1214,25 +1293,25 @@ __device__ __noinline__ void column_warp(const Dev &d, const VarOut &o, int q, S
     {
         const bool fl = dfinite(__ldg(d.lb + c.j)), fu = dfinite(__ldg(d.ub + c.j));
         if (lane == 0) {
-            if (fl) stage[0] = SEnt{c.kl, 0, make_aux(0, 0)};
-            if (fu) stage[fl ? 1 : 0] = SEnt{c.ku, 0, make_aux(0, 0)};
+            if (fl) stage[0] = SEnt{c.kl, 0, make_aux(kClsPre, 0)};
+            if (fu) stage[fl ? 1 : 0] = SEnt{c.ku, 0, make_aux(kClsPre, 0)};
         }
         cnt = (int)fl + (int)fu;
     }
     Acc acc{0, 0, 0, 0};
     for (int v = lane; v - lane < nv; v += 32) {
         Half h1, h2;
-        h1.type = 0;
-        h2.type = 0;
+        h1.type = 0; h1.mark = 0;
+        h2.type = 0; h2.mark = 0;
         if (v < nv) gen_entry(d, c, v, acc, h1, h2);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const Half &h = hh ? h2 : h1;
-            const bool has = h.type != 0;
+        for (int hh = 0; hh < 4; ++hh) {
+            const Half &h = (hh & 1) ? h2 : h1;
+            const bool has = hh < 2 ? h.type != 0 : h.mark != 0;
             const unsigned bal = __ballot_sync(FULLMASK, has);
             if (has)
                 stage[cnt + __popc(bal & ((1u << lane) - 1u))] =
-                    SEnt{h.key, (int)h.D, h.type == 1 ? make_aux(0, -1) : make_aux(1, 1)};
+                    hh < 2 ? SEnt{h.key, (int)h.D, half_aux(h)} : SEnt{h.mkey, 0, marker_aux()};
             cnt += __popc(bal);
         }
     }
@@ -1301,7 +1380,7 @@ __device__ __forceinline__ void nb_int_half(long long r, int a, int w, bool act,
     const bool left = z <= Lz, right = z > Rz;
     const bool dec = act && (left || right);
     acc_decided(dec ? (((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
-    enqueue(W, Q, act && !dec, QItem{r, (long long)a, w, L.g | ((int)V << 4)}, L.lane);
+    enqueue(W, Q, act && !dec, QItem{r, (long long)a, 0, w, L.g | ((int)V << 4)}, L.lane);
 }
 
 // Both loops below load the next round's row index and coefficient while the
@@ -1331,24 +1410,30 @@ __device__ __forceinline__ void nb_int_part(const Dev &d, int e0, int n, int nma
 }
 
 // One half of a non-integral row: residual r, coefficient a, margins m = eps - r
-// of the half and mo of the other half.  Integer variable: z = m; continuous:
-// z = -r; the breakpoint is placed by float products with margins, and
-// |r| <= eps makes the half tight wherever t is.
+// of the half and mo of the other half.  Integer variable: its breakpoint
+// xbar + m / a is placed (z = m); continuous: both the tight point xbar - r / a
+// and the boundary xbar + m / a must lie on one side (z from -r to m).  The
+// points are placed by float products with margins.
 template <int G>
 __device__ __forceinline__ void nb_fp_half(double r, double a, double m, double mo, int w, bool act,
                                            const NbLane &L, NbWarp<G> &W, NbQueue &Q, Acc &acc)
 {
     const bool V = dneg(m), P = !dneg(a);
-    const bool T = !L.isint && !V && !dneg(mo);
-    const double z0 = L.isint ? m : dflip(r);
+    const bool near0 = !L.isint && !V && !dneg(mo);
+    // normalised (a > 0) offsets of the points: zb the boundary (the integer
+    // variable's breakpoint), zt the continuous variable's tight point; zt <= zb
+    // for a > 0 and zb <= zt for a < 0 since eps >= 0
+    const double zb = P ? m : dflip(m), zt = P ? dflip(r) : r;
+    const double zlo = (L.isint || !P) ? zb : zt, zhi = (L.isint || P) ? zb : zt;
     bool fin = L.fok;
-    const float zf = approx_f(P ? z0 : dflip(z0), fin), af = approx_f(P ? a : dflip(a), fin);
+    const float zl = approx_f(zlo, fin), zh = approx_f(zhi, fin), af = approx_f(P ? a : dflip(a), fin);
     bool left = false, right = false;
-    if (fin) side_test(zf, af, P ? L.Lp : L.Ln, P ? L.Up : L.Un, L.tolf * af, left, right);
-    const bool dec = act && (T || left || right);
-    acc_decided(dec ? (((int)T << 3) | ((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
+    if (fin) side_test(zl, zh, af, P ? L.Lp : L.Ln, P ? L.Up : L.Un, L.tolf * af, left, right);
+    const bool dec = act && (left || right);
+    acc_decided(dec ? (((int)P << 2) | ((int)V << 1) | (int)left) : 1, w, acc);
     enqueue(W, Q, act && !dec,
-            QItem{__double_as_longlong(L.isint ? m : r), __double_as_longlong(a), w, L.g | 8 | ((int)V << 4)},
+            QItem{__double_as_longlong(L.isint ? m : r), __double_as_longlong(a), __double_as_longlong(m), w,
+                  L.g | 8 | ((int)V << 4) | ((int)near0 << 5)},
             L.lane);
 }
 
@@ -1424,8 +1509,8 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
                 W.beta[g] = 0; W.alpha[g] = 0; W.beta_c[g] = 0; W.alpha_c[g] = 0;
                 int n = 0;
                 if (live) {
-                    if (dfinite(__ldg(d.lb + c.j))) W.stage[g * STG + n++] = SEnt{c.kl, 0, make_aux(0, 0)};
-                    if (dfinite(__ldg(d.ub + c.j))) W.stage[g * STG + n++] = SEnt{c.ku, 0, make_aux(0, 0)};
+                    if (dfinite(__ldg(d.lb + c.j))) W.stage[g * STG + n++] = SEnt{c.kl, 0, make_aux(kClsPre, 0)};
+                    if (dfinite(__ldg(d.ub + c.j))) W.stage[g * STG + n++] = SEnt{c.ku, 0, make_aux(kClsPre, 0)};
                 }
                 W.cnt[g] = n;
             }
@@ -1546,6 +1631,29 @@ __device__ __forceinline__ void block_scan2(long long &v, int &vc, long long *ws
     __syncthreads();
 }
 
+// Bitonic sort of N (a power of two) entries in shared memory by (t, class),
+// all threads of the CTA; ends with a barrier.
+__device__ void cta_bitonic(unsigned long long *skey, long long *sdel, unsigned *saux, int N)
+{
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
+                const int i = 2 * stride * (p / stride) + (p % stride);
+                const int k2 = i + stride;
+                const bool asc = (i & size) == 0;
+                unsigned long long ka = skey[i], kb = skey[k2];
+                unsigned aa = saux[i], ab = saux[k2];
+                if (entry_less(kb, ab, ka, aa) == asc) {
+                    skey[i] = kb; skey[k2] = ka;
+                    saux[i] = ab; saux[k2] = aa;
+                    long long t = sdel[i]; sdel[i] = sdel[k2]; sdel[k2] = t;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // One column per CTA, entries sorted in shared memory (bitonic, N = tile.aux).
 __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *tiles, VarOut o, int slot0, int gate)
 {
@@ -1568,8 +1676,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
     if (threadIdx.x == 0) {
         s_cnt = (fl ? 1 : 0) + (fu ? 1 : 0);
         s_beta = 0; s_alpha = 0; s_bc = 0; s_ac = 0;
-        if (fl) { skey[0] = c.kl; sdel[0] = 0; saux[0] = make_aux(0, 0); }
-        if (fu) { int p = fl ? 1 : 0; skey[p] = c.ku; sdel[p] = 0; saux[p] = make_aux(0, 0); }
+        if (fl) { skey[0] = c.kl; sdel[0] = 0; saux[0] = make_aux(kClsPre, 0); }
+        if (fu) { int p = fl ? 1 : 0; skey[p] = c.ku; sdel[p] = 0; saux[p] = make_aux(kClsPre, 0); }
     }
     __syncthreads();
     Acc acc{0, 0, 0, 0};
@@ -1577,7 +1685,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
     for (int v = threadIdx.x; v < total; v += blockDim.x) {
         Half h1, h2;
         gen_entry(d, c, v, acc, h1, h2);
-        const int n1 = h1.type != 0, n2 = h2.type != 0;
+        const int n1 = half_entries(h1), n2 = half_entries(h2);
         if (n1 + n2) {
             int pos = atomicAdd(&s_cnt, n1 + n2);
             if (n1) put_half(h1, pos, skey, sdel, saux);
@@ -1593,25 +1701,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
     }
     __syncthreads();
     const int cnt = s_cnt;
-    for (int i = cnt + threadIdx.x; i < N; i += blockDim.x) { skey[i] = kPadKey; sdel[i] = 0; saux[i] = make_aux(1, 0); }
+    for (int i = cnt + threadIdx.x; i < N; i += blockDim.x) { skey[i] = kPadKey; sdel[i] = 0; saux[i] = make_aux(kClsPost, 0); }
     __syncthreads();
-    for (int size = 2; size <= N; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
-                const int i = 2 * stride * (p / stride) + (p % stride);
-                const int k2 = i + stride;
-                const bool asc = (i & size) == 0;
-                unsigned long long ka = skey[i], kb = skey[k2];
-                unsigned aa = saux[i], ab = saux[k2];
-                if (entry_less(kb, ab, ka, aa) == asc) {
-                    skey[i] = kb; skey[k2] = ka;
-                    saux[i] = ab; saux[k2] = aa;
-                    long long t = sdel[i]; sdel[i] = sdel[k2]; sdel[k2] = t;
-                }
-            }
-            __syncthreads();
-        }
-    }
+    cta_bitonic(skey, sdel, saux, N);
     const int per = N / blockDim.x;
     const int b0 = threadIdx.x * per;
     long long run = 0;
@@ -1630,9 +1722,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_eval_cta(Dev d, const Tile *til
         P += sdel[i];
         Pc += aux_dc(a);
         const unsigned long long knext = i + 1 < N ? skey[i + 1] : kPadKey;
-        const unsigned anext = i + 1 < N ? saux[i + 1] : make_aux(1, 0);
+        const unsigned anext = i + 1 < N ? saux[i + 1] : make_aux(kClsPost, 0);
         const unsigned long long kprev = i > 0 ? skey[i - 1] : 0ull;
-        if (!is_candidate(kk, a, kprev, i > 0, knext, anext)) continue;
+        const unsigned aprev = i > 0 ? saux[i - 1] : 0u;
+        if (!is_candidate(kk, a, kprev, aprev, i > 0, knext, anext)) continue;
         const bool post = aux_post(a) != 0;
         const long long Pi = P - (post ? sdel[i] : 0);
         const int Pci = Pc - (post ? aux_dc(a) : 0);
@@ -1751,6 +1844,243 @@ __global__ void __launch_bounds__(kHistThreads) k_eval_hist(Dev d, const Tile *t
     finish_pass(d);
 }
 
+// ------------------------------------ multi-CTA merge sort (long lists)
+//
+// Lists longer than one CTA sorts (Sec. 3.1, "Kernel Specialization": long
+// vectors need grid-wide primitives).  k_long_gen: one CTA per chunk of
+// kLongChunk nonzeros generates the chunk's entries (and the bounds in chunk
+// 0), sorts them in shared memory and writes a run of kLongRun entries padded
+// with pad keys (pad runs fill the column up to a power of two); the
+// accumulators beta / alpha go to the column's global accumulator.
+// k_long_merge: one pairwise merge round over all columns, one thread per
+// output entry placed by a merge-path binary search (stable: the left run
+// first on equal (t, class)).  k_long_tilesum / k_long_eval: the merged list is
+// scanned in tiles of kLongTile entries; each tile adds the sums of the tiles
+// before it (its carry), evaluates its candidates (neighbours read across tile
+// edges) and the last tile of the column reduces the tiles' candidates.
+
+__global__ void __launch_bounds__(kLongThreads) k_long_gen(Dev d, const Tile *tiles, int gate)
+{
+    if (gated_done(d, gate)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *skey = reinterpret_cast<unsigned long long *>(smem);
+    long long *sdel = reinterpret_cast<long long *>(skey + kLongRun);
+    unsigned *saux = reinterpret_cast<unsigned *>(sdel + kLongRun);
+    __shared__ int s_cnt;
+    const Tile tl = tiles[blockIdx.x];
+    const LongCol lc = d.lcols[tl.begin];
+    const int chunk = tl.aux;
+    const ColCtx c = make_col(d, lc.pos, d.ctl->iter);
+    if (threadIdx.x == 0) {
+        int n0 = 0;
+        if (chunk == 0) {
+            if (dfinite(__ldg(d.lb + c.j))) { skey[n0] = c.kl; sdel[n0] = 0; saux[n0] = make_aux(kClsPre, 0); ++n0; }
+            if (dfinite(__ldg(d.ub + c.j))) { skey[n0] = c.ku; sdel[n0] = 0; saux[n0] = make_aux(kClsPre, 0); ++n0; }
+        }
+        s_cnt = n0;
+    }
+    __syncthreads();
+    Acc acc{0, 0, 0, 0};
+    if (chunk < lc.nchunks) {
+        const int v0 = chunk * kLongChunk, v1 = min(lc.e_end, v0 + kLongChunk);
+        for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            Half h1, h2;
+            gen_entry(d, c, v, acc, h1, h2);
+            const int n1 = half_entries(h1), n2 = half_entries(h2);
+            if (n1 + n2) {
+                const int pos = atomicAdd(&s_cnt, n1 + n2);
+                if (n1) put_half(h1, pos, skey, sdel, saux);
+                if (n2) put_half(h2, pos + n1, skey, sdel, saux);
+            }
+        }
+    }
+    warp_allreduce_acc(acc);
+    HistAcc *la = d.lacc + tl.begin;
+    if ((threadIdx.x & 31) == 0 && (acc.beta | acc.alpha | acc.beta_c | acc.alpha_c)) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&la->beta), (unsigned long long)acc.beta);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&la->alpha), (unsigned long long)acc.alpha);
+        atomicAdd(&la->beta_c, acc.beta_c);
+        atomicAdd(&la->alpha_c, acc.alpha_c);
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int i = cnt + threadIdx.x; i < kLongRun; i += blockDim.x) {
+        skey[i] = kPadKey; sdel[i] = 0; saux[i] = make_aux(kClsPost, 0);
+    }
+    __syncthreads();
+    cta_bitonic(skey, sdel, saux, kLongRun);
+    SEntry *out = d.lbuf0 + lc.base + (long long)chunk * kLongRun;
+    for (int i = threadIdx.x; i < kLongRun; i += blockDim.x) out[i] = SEntry{skey[i], (int)sdel[i], saux[i]};
+}
+
+__device__ __forceinline__ bool sent_less(const SEntry &a, const SEntry &b) { return entry_less(a.key, a.aux, b.key, b.aux); }
+
+// One merge round: runs of `width` entries merged pairwise (columns already
+// merged into one run are copied).
+__global__ void __launch_bounds__(256) k_long_merge(Dev d, const SEntry *in, SEntry *out, long long width,
+                                                    long long total, int gate)
+{
+    if (gated_done(d, gate)) return;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = d.n_long - 1;   // the column with base <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d.lcols[mid].base <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const LongCol &lc = d.lcols[lo];
+        const long long k = e - lc.base;
+        if ((long long)lc.runs * kLongRun <= width) {
+            out[e] = in[e];
+            continue;
+        }
+        const long long p0 = lc.base + (k / (2 * width)) * 2 * width;
+        const long long kk = k % (2 * width);
+        const SEntry *A = in + p0, *B = in + p0 + width;
+        // smallest i with B[kk - i - 1] < A[i]: the number of A entries among
+        // the first kk outputs
+        long long a = kk > width ? kk - width : 0, b = kk < width ? kk : width;
+        while (a < b) {
+            const long long i = (a + b) >> 1;
+            const long long j = kk - i - 1;
+            if (j < 0 || sent_less(B[j], A[i])) b = i;
+            else a = i + 1;
+        }
+        const long long i = a, j = kk - a;
+        out[e] = (i < width && (j >= width || !sent_less(B[j], A[i]))) ? A[i] : B[j];
+    }
+}
+
+__global__ void __launch_bounds__(kLongThreads) k_long_tilesum(Dev d, const SEntry *buf, const Tile *tiles, int gate)
+{
+    if (gated_done(d, gate)) return;
+    const Tile tl = tiles[blockIdx.x];
+    const LongCol lc = d.lcols[tl.begin];
+    const SEntry *p = buf + lc.base + (long long)tl.aux * kLongTile;
+    long long s = 0;
+    int sc = 0;
+    for (int i = threadIdx.x; i < kLongTile; i += blockDim.x) {
+        s += p[i].del;
+        sc += aux_dc(p[i].aux);
+    }
+    __shared__ long long ws[32];
+    __shared__ int wsc[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(FULLMASK, s, o);
+        sc += __shfl_xor_sync(FULLMASK, sc, o);
+    }
+    if ((threadIdx.x & 31) == 0) { ws[threadIdx.x >> 5] = s; wsc[threadIdx.x >> 5] = sc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        int tc = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += ws[w]; tc += wsc[w]; }
+        d.ltsum[lc.tile0 + tl.aux] = t;
+        d.ltsumc[lc.tile0 + tl.aux] = tc;
+    }
+}
+
+__global__ void __launch_bounds__(kLongThreads) k_long_eval(Dev d, const SEntry *buf, const Tile *tiles, VarOut o,
+                                                            int gate)
+{
+    if (gated_done(d, gate)) return;
+    __shared__ long long wsum[32];
+    __shared__ int wsumc[32];
+    __shared__ int s_last;
+    const Tile tl = tiles[blockIdx.x];
+    const LongCol lc = d.lcols[tl.begin];
+    const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
+    const ColCtx c = make_col(d, lc.pos, iter);
+    const long long len = (long long)lc.runs * kLongRun;
+    // carry: the sums of the column's earlier tiles (block reduction)
+    __shared__ long long s_carry;
+    __shared__ int s_carryc;
+    {
+        long long cs = 0;
+        int csc = 0;
+        for (int t = threadIdx.x; t < tl.aux; t += blockDim.x) {
+            cs += __ldcg(d.ltsum + lc.tile0 + t);
+            csc += __ldcg(d.ltsumc + lc.tile0 + t);
+        }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            cs += __shfl_xor_sync(FULLMASK, cs, o2);
+            csc += __shfl_xor_sync(FULLMASK, csc, o2);
+        }
+        if ((threadIdx.x & 31) == 0) { wsum[threadIdx.x >> 5] = cs; wsumc[threadIdx.x >> 5] = csc; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            int tc = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += wsum[w]; tc += wsumc[w]; }
+            s_carry = t;
+            s_carryc = tc;
+        }
+        __syncthreads();
+    }
+    const long long carry_all = s_carry;
+    const int carryc_all = s_carryc;
+    const HistAcc *la = d.lacc + tl.begin;
+    const long long beta = __ldcg(&la->beta), alpha = __ldcg(&la->alpha);
+    const int bc = __ldcg(&la->beta_c), ac = __ldcg(&la->alpha_c);
+    constexpr int per = kLongTile / kLongThreads;
+    const long long t0 = lc.base + (long long)tl.aux * kLongTile;
+    const long long i0 = (long long)tl.aux * kLongTile + threadIdx.x * per;   // index inside the column
+    long long run = 0;
+    int runc = 0;
+    for (int q = 0; q < per; ++q) {
+        const SEntry &e = buf[t0 + threadIdx.x * per + q];
+        run += e.del;
+        runc += aux_dc(e.aux);
+    }
+    long long P = run;
+    int Pc = runc;
+    block_scan2(P, Pc, wsum, wsumc);
+    P += carry_all;
+    Pc += carryc_all;
+    VCand vb{0, 0ull, 0, 0};
+    for (int q = 0; q < per; ++q) {
+        const long long i = i0 + q;
+        const SEntry e = buf[lc.base + i];
+        P += e.del;
+        Pc += aux_dc(e.aux);
+        const SEntry nx = i + 1 < len ? buf[lc.base + i + 1] : SEntry{kPadKey, 0, make_aux(kClsPost, 0)};
+        const SEntry pv = i > 0 ? buf[lc.base + i - 1] : SEntry{0ull, 0, 0u};
+        if (!is_candidate(e.key, e.aux, pv.key, pv.aux, i > 0, nx.key, nx.aux)) continue;
+        const bool post = aux_post(e.aux) != 0;
+        const long long Pi = P - (post ? e.del : 0);
+        const int Pci = Pc - (post ? aux_dc(e.aux) : 0);
+        const bool right = e.key > c.kxb;
+        consider(vb, c, e.key, beta + Pi + (right ? alpha : 0), bc + Pci + (right ? ac : 0), nviol, bestnv);
+    }
+    vb = block_reduce_vc(vb, c);
+    HistAcc *law = d.lacc + tl.begin;
+    if (threadIdx.x == 0) {
+        d.lcand[lc.tile0 + tl.aux] = LCand{vb.s, vb.key, vb.dc, vb.valid};
+        __threadfence();
+        s_last = atomicAdd(&law->ticket, 1u) == (unsigned)(lc.ntiles - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    VCand b{0, 0ull, 0, 0};
+    for (int t = threadIdx.x; t < lc.ntiles; t += blockDim.x) {
+        const LCand *p = d.lcand + lc.tile0 + t;
+        const VCand v{__ldcg(&p->s), __ldcg(&p->key), __ldcg(&p->dc), __ldcg(&p->valid)};
+        if (vc_better(v, b, c)) b = v;
+    }
+    b = block_reduce_vc(b, c);
+    if (threadIdx.x == 0) {
+        Cand best{0, kNoVar, 0, 0.0};
+        finish_column(d, o, c, b, best);
+        d.block_best[lc.slot] = best;
+        *law = HistAcc{0, 0, 0, 0, 0u, 0};
+    }
+    finish_pass(d);
+}
+
 // Default of every per-variable output (fixed variables keep it).
 __global__ void k_fill_outputs(Dev d, VarOut o)
 {
@@ -1787,6 +2117,51 @@ __global__ void __launch_bounds__(1024) k_select(Dev d, int gate)
             c->mv_new = 0.0;
             c->mv_old = 0.0;
         }
+    }
+}
+
+// The move selected by the last pass as an exchange record.
+__global__ void k_move_record(Dev d, chap_move_record *rec)
+{
+    const Ctl *c = d.ctl;
+    chap_move_record r;
+    r.score_half = c->mv_var >= 0 ? c->mv_s : 0;
+    r.var = c->mv_var;
+    r.dnviol = c->mv_dc;
+    r.new_value = c->mv_new;
+    r.old_value = c->mv_old;
+    *rec = r;
+}
+
+// The winner of k shards' records (largest score, then lowest variable; no
+// positive score: the weight update) becomes the iteration's move.
+__global__ void k_apply_records(Dev d, const chap_move_record *recs, int k)
+{
+    long long bs = 0;
+    int bv = kNoVar, bdc = 0;
+    double bnew = 0.0;
+    for (int q = 0; q < k; ++q) {
+        const chap_move_record r = recs[q];
+        if (r.score_half > 0 && r.var >= 0 && r.var < d.n && cand_better(r.score_half, r.var, bs, bv)) {
+            bs = r.score_half;
+            bv = r.var;
+            bdc = r.dnviol;
+            bnew = r.new_value;
+        }
+    }
+    Ctl *c = d.ctl;
+    if (bv != kNoVar) {
+        c->mv_var = bv;
+        c->mv_s = bs;
+        c->mv_dc = bdc;
+        c->mv_new = bnew;
+        c->mv_old = d.x[bv];
+    } else {
+        c->mv_var = -1;
+        c->mv_s = 0;
+        c->mv_dc = 0;
+        c->mv_new = 0.0;
+        c->mv_old = 0.0;
     }
 }
 
@@ -2137,6 +2512,23 @@ __global__ void k_unpack_r(Dev d, double *r)
     }
 }
 
+// Objective c^T x of the current assignment into *out: one CTA, a strided
+// partial sum per thread and a fixed reduction tree (the same value on every
+// call for the same x).
+__global__ void __launch_bounds__(1024) k_objective(Dev d, double *out)
+{
+    __shared__ double part[1024];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < d.n; j += blockDim.x) s = __dadd_rn(s, __dmul_rn(d.obj[j], d.x[j]));
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] = __dadd_rn(part[threadIdx.x], part[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
 __global__ void k_widen(int n, const int *a, long long *b)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) b[j] = a[j];
@@ -2151,6 +2543,8 @@ static int grid_for(long long n, int threads, int cap = 152 * 8)
     if (g > cap) g = cap;
     return (int)g;
 }
+
+static cudaError_t raise_smem_limit(const void *fn, int slot, int bytes);
 
 int bin_grid_size(int ncols, int G)
 {
@@ -2179,7 +2573,7 @@ int nb_grid_size(int ncols, int G)
     int per_sm = 0;
     const void *fn = G == 4 ? (const void *)k_eval_nb<4> : (const void *)k_eval_nb<8>;
     const int smem = G == 4 ? nb_smem<4>() : nb_smem<8>();
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+    if (raise_smem_limit(fn, G == 4 ? 0 : 1, smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kEvalThreads, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -2205,14 +2599,18 @@ static __device__ __align__(256) HistAcc g_static_acc[kStaticHistCols];
 
 cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc)
 {
-    // resolved once per device, with that device current
+    // resolved once per device, with that device current; the cache is read
+    // and written under a mutex, so first calls from several host threads do
+    // not race on it
     constexpr int kMaxDevices = 64;
+    static std::mutex s_mu;
     static HBin *s_bins[kMaxDevices] = {};
     static HistAcc *s_acc[kMaxDevices] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(s_mu);
     if (!s_bins[dev] || !s_acc[dev]) {
         void *pb = nullptr, *pa = nullptr;
         e = cudaGetSymbolAddress(&pb, g_static_bins);
@@ -2227,17 +2625,56 @@ cudaError_t static_hist_scratch(HBin **bins, HistAcc **acc)
     return cudaSuccess;
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel, shared by
+// every handle of the process on a device: it is only ever raised (to the
+// largest size any handle launches with), under a mutex.
+static cudaError_t raise_smem_limit(const void *fn, int slot, int bytes)
+{
+    constexpr int kMaxDevices = 64, kSlots = 8;
+    static std::mutex s_mu;
+    static int s_set[kMaxDevices][kSlots] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(s_mu);
+    if (bytes <= s_set[dev][slot]) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) s_set[dev][slot] = bytes;
+    return e;
+}
+
 cudaError_t setup_kernel_attributes(const LaunchPlan &p)
 {
     cudaError_t e = cudaSuccess;
     if (p.nb_grid > 0)
-        e = p.nb_G == 4 ? cudaFuncSetAttribute(k_eval_nb<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb_smem<4>())
-                        : cudaFuncSetAttribute(k_eval_nb<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb_smem<8>());
-    if (e == cudaSuccess && p.cta_smem > 0)
-        e = cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, p.cta_smem);
-    if (e == cudaSuccess && p.hist_smem > 0)
-        e = cudaFuncSetAttribute(k_eval_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, p.hist_smem);
+        e = p.nb_G == 4 ? raise_smem_limit((const void *)k_eval_nb<4>, 0, nb_smem<4>())
+                        : raise_smem_limit((const void *)k_eval_nb<8>, 1, nb_smem<8>());
+    if (e == cudaSuccess && p.cta_smem > 0) e = raise_smem_limit((const void *)k_eval_cta, 2, p.cta_smem);
+    if (e == cudaSuccess && p.hist_smem > 0) e = raise_smem_limit((const void *)k_eval_hist, 3, p.hist_smem);
+    if (e == cudaSuccess && p.n_lgen > 0) e = raise_smem_limit((const void *)k_long_gen, 4, long_gen_smem());
     return e;
+}
+
+int long_gen_smem() { return kLongRun * (int)(sizeof(unsigned long long) + sizeof(long long) + sizeof(unsigned)); }
+
+// The long lists' kernels on `st`: generation and run sort, the merge rounds,
+// the tile sums and the scan / argmax.
+static cudaError_t launch_long(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st)
+{
+    k_long_gen<<<p.n_lgen, kLongThreads, long_gen_smem(), st>>>(d, p.tiles_lgen, gate);
+    const SEntry *in = d.lbuf0;
+    SEntry *out = d.lbuf1;
+    const int grid = (int)std::min<long long>(152 * 8, (p.long_entries + 255) / 256);
+    for (int r = 0; r < p.long_rounds; ++r) {
+        k_long_merge<<<grid, 256, 0, st>>>(d, in, out, (long long)kLongRun << r, p.long_entries, gate);
+        const SEntry *t = out;
+        out = const_cast<SEntry *>(in);
+        in = t;
+    }
+    k_long_tilesum<<<p.n_lscan, kLongThreads, 0, st>>>(d, in, p.tiles_lscan, gate);
+    k_long_eval<<<p.n_lscan, kLongThreads, 0, st>>>(d, in, p.tiles_lscan, o, gate);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st)
@@ -2247,7 +2684,7 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     // selection.  The same fork/join shape is recorded by graph capture.
     if (o.xhat || o.s || o.dc) k_fill_outputs<<<grid_for(d.n, 256), 256, 0, st>>>(d, o);
     cudaError_t e = cudaEventRecord(p.ev_fork, st);
-    const bool side[3] = {p.nb_grid > 0, p.n_cta > 0, p.n_hist_tiles > 0};
+    const bool side[3] = {p.nb_grid > 0, p.n_cta > 0 || p.n_lgen > 0, p.n_hist_tiles > 0};
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (side[k]) e = cudaStreamWaitEvent(p.side[k], p.ev_fork, 0);
     if (e != cudaSuccess) return e;
@@ -2282,9 +2719,10 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
             k_eval_nb<8><<<p.nb_grid, kEvalThreads, nb_smem<8>(), p.side[0]>>>(d, p.nb_q0, p.nb_cols, o, p.slot_nb, gate);
         PROF(1, 1);
     }
-    if (p.n_cta) {
+    if (p.n_cta || p.n_lgen) {
         PROF(2, 0);
-        k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
+        if (p.n_cta) k_eval_cta<<<p.n_cta, kCtaThreads, p.cta_smem, p.side[1]>>>(d, p.tiles_cta, o, p.slot_cta, gate);
+        if (p.n_lgen && e == cudaSuccess) e = launch_long(d, p, o, gate, p.side[1]);
         PROF(2, 1);
     }
     if (p.n_hist_tiles) {
@@ -2370,6 +2808,24 @@ cudaError_t launch_unpack_w(const Dev &d, int *w, cudaStream_t st)
 cudaError_t launch_unpack_r(const Dev &d, double *r, cudaStream_t st)
 {
     k_unpack_r<<<grid_for(d.m, 256), 256, 0, st>>>(d, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_move_record(const Dev &d, chap_move_record *rec, cudaStream_t st)
+{
+    k_move_record<<<1, 1, 0, st>>>(d, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_records(const Dev &d, const chap_move_record *recs, int k, cudaStream_t st)
+{
+    k_apply_records<<<1, 1, 0, st>>>(d, recs, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const Dev &d, double *out, cudaStream_t st)
+{
+    k_objective<<<1, 1024, 0, st>>>(d, out);
     return cudaGetLastError();
 }
 

@@ -887,6 +887,7 @@ chap_status chap_bs_refresh_features(chap_bs *h)
 {
     if (!h) return CHAP_E_INVALID;
     if (h->broken) return lfail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
+    if (own_scratch_ok(h) != CHAP_OK || whole_instance_ok(h) != CHAP_OK) return CHAP_E_STATE;
     LearnHost *lh = nullptr;
     chap_status s = ensure_learn(h, &lh);
     if (s != CHAP_OK) return lfail(h, s, "learned-driver state");
@@ -944,6 +945,7 @@ chap_status chap_learned_run(chap_bs *h, const uint16_t *weights, const chap_lea
     if (h->broken) return lfail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
     if (lo->topk < 1 || lo->exact_every < 1 || lo->propose_every < 1 || lo->max_iters < 0)
         return lfail(h, CHAP_E_INVALID, "bad learned-run options");
+    if (own_scratch_ok(h) != CHAP_OK || whole_instance_ok(h) != CHAP_OK) return CHAP_E_STATE;
     if (h->info.n_bin != h->n - h->info.n_fixed || h->n >= (1 << kVarBits))
         return lfail(h, CHAP_E_UNSUPPORTED, "the learned driver handles all-binary instances below 2^22 variables");
     LearnHost *lh = nullptr;

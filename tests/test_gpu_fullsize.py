@@ -1,8 +1,8 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (one handle, full passes), on sampled variables the oracle evaluates one
-by one: the general 200k-var MIP (non-integral rows: scores equal, shifts within
-1e-9 relative, a handful of tolerance-window cases allowed) and the skewed 2M-var
-MIP (all rows integral: bit-exact, every dense column included)."""
+by one: the general 200k-var MIP (non-integral rows: scores and violation
+changes equal, shifts within 1e-9 relative, state-fed after the run) and the
+skewed 2M-var MIP (all rows integral: bit-exact, every dense column included)."""
 import numpy as np
 import pytest
 
@@ -30,6 +30,15 @@ def _sampled(chap, prob, vars_, states, exact):
     for it in states:
         if it:
             bs.run(max_iters=it, stop_at_feasible=0)
+            if not exact:
+                # state-fed: the device recomputes the residuals of the state it
+                # reached (incremental FP64 residuals drift by rounding; the drift
+                # is checked below), as the oracle does
+                r_inc = bs.residuals()
+                r_def, _, _ = orc.residuals(bs.state()["x"])
+                b = np.abs(orc.norm_rows()[2])
+                assert np.all(np.abs(r_inc - r_def) <= 1e-9 * np.maximum(1.0, b))
+                bs.set_checkpoint(bs.state())
         st = bs.state()
         _, _, nv = orc.residuals(st["x"])
         assert nv == st["nviol"]
@@ -53,7 +62,7 @@ def test_general_200k_sampled(chap):
     vt = prob.vtype
     vars_ = np.unique(np.concatenate([rng.choice(np.nonzero(vt == t)[0], 1500, replace=False) for t in (0, 1, 2)]))
     bad = _sampled(chap, prob, vars_.astype(np.int32), [0, 100], exact=False)
-    assert bad <= 4, bad
+    assert bad == 0, bad
 
 
 def test_skewed_2m_sampled(chap):

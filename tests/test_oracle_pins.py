@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from conftest import golden_cases, problem_from_case
+from conftest import fp_tiny, golden_cases, problem_from_case
 from oracle import definition
 from oracle.oracle import Oracle
 from paper_2605_05086_gb300 import instances as inst
@@ -138,6 +138,71 @@ def test_continuous_grid_never_beats_best(seed):
             s, d = definition.score(rows, xf, w, j, g)
             if definition.admissible(g, xf[j], j, d, ti, td, it, nviol, bn):
                 assert s <= max(int(sh[j]), 0), (j, g, s, sh[j])
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_continuous_grid_with_tolerance_exact_classification(seed):
+    """feas_tol = 1e-9 on N(0,1) rows, every classification in exact rationals
+    (violated iff r > eps): the oracle's score is the exact score of its value;
+    it is the best admissible score over the exact candidate set (finite bounds
+    and the tight points of rows not satisfied within eps -- a row with
+    |r| <= eps contributes none), its value is that set's tie-break winner (largest
+    score, smallest |x - xbar|, smaller x) up to the rounding of the breakpoint;
+    and no point of a dense grid of [l, u] or next to a candidate scores
+    higher."""
+    tol = 1e-9
+    prob, x = fp_tiny(seed, tol)
+    rng = np.random.default_rng(4000 + seed)
+    orc = Oracle(prob, feas_tol=tol)
+    w = rng.integers(1, 4, size=orc.mn).astype(np.int32)
+    it = 2
+    ti, td = _random_tabu(rng, prob.n, it)
+    _, _, nviol = orc.residuals(x)
+    exact_r, exact_v, exact_nv = definition.residual_state(prob, x, tol)
+    assert nviol == exact_nv
+    bn = nviol - int(rng.integers(0, 2))
+    xh, sh, dc = orc.best_shift(x, w, ti, td, it, nviol, bn)
+    rows = definition.normalised_rows(prob, tol)
+    xf = [F(float(v)) for v in x]
+    for j in range(prob.n):
+        if prob.vtype[j] != inst.VAR_CONT:
+            continue
+        scored = []
+        for c in definition.candidate_values(prob, x, j, tol):
+            s, d = definition.score(rows, xf, w, j, c)
+            if definition.admissible(c, xf[j], j, d, ti, td, it, nviol, bn):
+                scored.append((s, c, d))
+        best = max([s for s, _, _ in scored], default=None)
+        if best is None or best <= 0:
+            assert (float(xh[j]), int(sh[j]), int(dc[j])) == (float(x[j]), 0, 0), j
+        else:
+            win = min((c for s, c, _ in scored if s == best), key=lambda c: (abs(c - xf[j]), c))
+            assert int(sh[j]) == best, (j, int(sh[j]), best)
+            assert abs(F(float(xh[j])) - win) <= F(1, 10**12) * max(F(1), abs(win)), (j, float(xh[j]), float(win))
+            s, d = definition.score(rows, xf, w, j, F(float(xh[j])))
+            assert (s, d) == (int(sh[j]), int(dc[j])), j
+        lo, hi = F(float(prob.lb[j])), F(float(prob.ub[j]))
+        pts = [lo + (hi - lo) * F(q, 400) for q in range(401)]
+        for _, c, _ in scored:
+            pts += [c - F(1, 10**4), c + F(1, 10**4)]
+        for g in pts:
+            if g == xf[j] or not lo <= g <= hi:
+                continue
+            s, d = definition.score(rows, xf, w, j, g)
+            if definition.admissible(g, xf[j], j, d, ti, td, it, nviol, bn):
+                assert s <= max(int(sh[j]), 0), (j, float(g), s, int(sh[j]))
+
+
+def test_fp_tiny_states_exercise_the_tolerance():
+    """The generator above does produce rows satisfied within eps but not
+    exactly tight (0 < |r| <= eps), the case the tight-row rule is about."""
+    hits = 0
+    for seed in range(80):
+        prob, x = fp_tiny(seed, 1e-9)
+        r, _, _ = definition.residual_state(prob, x, 1e-9)
+        for rk, (_, _, eps) in zip(r, definition.normalised_rows(prob, 1e-9)):
+            hits += int(0 < abs(rk) <= eps)
+    assert hits >= 20, hits
 
 
 @pytest.mark.parametrize("seed", range(20))
