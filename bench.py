@@ -204,7 +204,21 @@ def run_batch(args):
     t_e2e = time.perf_counter()
     b = chap.BatchChains(probs, chain_prob, tenures, stream=stream)
     t_create = time.perf_counter() - t_e2e
-    sched = b.autotune(iters=3)
+    # each schedule (three launches per iteration, one persistent launch per
+    # 64 iterations) autotuned on the batch and run to the cap; the faster one
+    # is the reported value, the other is kept for comparison
+    runs = {}
+    for mode in (0, 1):
+        sch = b.autotune(iters=20, mode=mode)
+        r_m, s_m = b.run(max_iters=args.batch_cap, stop_at_feasible=True, graph_iters=64)
+        runs[mode] = {"schedule": list(sch), "seconds": s_m, "moves": sum(r.moves for r in r_m),
+                      "moves_per_s": sum(r.moves for r in r_m) / s_m}
+        b.reset()
+    best_mode = max(runs, key=lambda k: runs[k]["moves_per_s"])
+    sched = tuple(runs[best_mode]["schedule"])
+    other = runs[1 - best_mode]
+    b.set_schedule(sched[0], sched[1])
+    b.set_persistent(sched[2])
     clocks = Clocks(torch.cuda.current_device())
     torch.cuda.synchronize()
     clocks.start()
@@ -235,7 +249,9 @@ def run_batch(args):
         "config": {"workload": "batch_64x4", "instances": 64, "chains": 256, "tenures": [5, 20, 35, 50],
                    "vars_total": sum(p.n for p in probs), "nnz_total": sum(p.nnz for p in probs),
                    "iteration_cap_per_chain": args.batch_cap, "schedule": {"lanes_per_column": sched[0],
-                                                                            "ctas_per_sm": sched[1]},
+                                                                            "ctas_per_sm": sched[1],
+                                                                            "persistent": sched[2]},
+                   "other_schedule": other,
                    "iters_total": iters, "moves_total": moves, "chains_feasible": len(feas_chains),
                    "instances_feasible": len(feas_inst),
                    "one_by_one": {"seconds": one_s, "moves": one_moves, "moves_per_s": one_moves / one_s,
@@ -244,7 +260,7 @@ def run_batch(args):
         "e2e": {"value": moves / e2e_s, "unit": "moves/s", "h2d_bytes_per_step": int(sum(
                     24 * p.nnz + 8 * p.m + 40 * p.n for p in probs)), "d2h_bytes_per_step": 256 * 48,
                 "call": "chap_batch_create (host instances) + chap_batch_run + per-chain results to host"},
-        "gpu_launches": 1 + 3 * 64 * ((max(r.iters for r in res) + 63) // 64),
+        "gpu_launches": 1 + (1 if sched[2] else 3 * 64) * ((max(r.iters for r in res) + 63) // 64),
         "clocks": clk,
     }
     print(json.dumps(line))

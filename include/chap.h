@@ -371,7 +371,8 @@ CHAP_API chap_status chap_bs_get_cutoff(struct chap_bs *h, chap_cutoff_info *inf
  * Batched tabu chains (growth path; Sec. 3.1, "Parallel Tabu Search Instances").
  * Many independent chains over several instances advance together: one
  * evaluation launch covers every (chain, 32-column tile), then one apply CTA
- * per chain and one weight-bump launch; K iterations are captured into one
+ * per chain and one weight-bump launch (or the three phases in one persistent
+ * launch, see chap_batch_set_persistent); K iterations are captured into one
  * CUDA graph and replayed.  Each chain follows exactly the single-handle
  * iteration (chap_bs_step) of its instance with its own tenure, from
  * x0 = 0, unit weights, no tabu.  Supported instances: every variable binary,
@@ -385,9 +386,24 @@ CHAP_API chap_status chap_bs_get_cutoff(struct chap_bs *h, chap_cutoff_info *inf
  *   per graph replay; res[n_chains] (host, optional) receives per-chain
  *   counters (chap_chain_result), *seconds (optional) the wall time.
  * chap_batch_autotune: times every schedule (lanes per column 2 / 4 / 8 / 16 x
- *   CTAs per SM 2 / 4 / 8) for `iters` iterations from the initial state, keeps
- *   the fastest (chosen[2] host, optional) and restores the initial state.
- * chap_batch_set_schedule: sets the schedule explicitly.
+ *   CTAs per SM 2 / 4 / 8 x three launches per iteration or one persistent
+ *   launch) for `iters` iterations from the initial state, keeps the fastest
+ *   (chosen[3] host, optional: lanes, CTAs per SM, persistent) and restores the
+ *   initial state.
+ * chap_batch_autotune_mode: the same over one schedule only (mode 0: three
+ *   launches per iteration, 1: persistent, -1: both).
+ * chap_batch_set_schedule: sets lanes per column and CTAs per SM explicitly.
+ * chap_batch_set_persistent: on = 1 runs each graph segment of K iterations as
+ *   one persistent cooperative launch (every CTA resident) whose phases (eval,
+ *   apply, bump) are separated by software grid barriers; on = 0 uses three
+ *   launches per iteration.  barrier_limit_ns > 0 bounds each barrier wait
+ *   (default 2 s; 0 keeps the current bound): a wait that runs out ends the
+ *   launch, chap_batch_run returns CHAP_E_TIMEOUT and the chains' state is
+ *   invalid until chap_batch_reset.  Default: persistent.
+ * The incumbents x of every chain are bitsets (one bit per variable); every
+ *   launch carries an L2 access-policy window that keeps them persisting in L2
+ *   (Sec. 3.1, "Memory Considerations", fourth point); the batch raises the
+ *   process's persisting-L2 set-aside to their size while it lives.
  * chap_batch_reset: every chain back to its initial state.
  * chap_batch_get_x: x of one chain (host double[n of its instance]).
  */
@@ -403,7 +419,9 @@ CHAP_API chap_status chap_batch_destroy(struct chap_batch *b);
 CHAP_API chap_status chap_batch_run(struct chap_batch *b, int64_t max_iters, int32_t stop_at_feasible,
                                     int32_t graph_iters, chap_chain_result *res, double *seconds);
 CHAP_API chap_status chap_batch_autotune(struct chap_batch *b, int32_t iters, int32_t *chosen);
+CHAP_API chap_status chap_batch_autotune_mode(struct chap_batch *b, int32_t iters, int32_t mode, int32_t *chosen);
 CHAP_API chap_status chap_batch_set_schedule(struct chap_batch *b, int32_t lanes_per_column, int32_t ctas_per_sm);
+CHAP_API chap_status chap_batch_set_persistent(struct chap_batch *b, int32_t on, int64_t barrier_limit_ns);
 CHAP_API chap_status chap_batch_reset(struct chap_batch *b);
 CHAP_API chap_status chap_batch_get_x(struct chap_batch *b, int32_t chain, double *x);
 CHAP_API const char *chap_batch_last_error(const struct chap_batch *b);

@@ -29,7 +29,7 @@ EXPORTED = [
     "chap_batch_reset", "chap_batch_get_x", "chap_batch_last_error",
     "chap_bs_refresh_features", "chap_bs_features", "chap_bs_propose", "chap_learned_run", "chap_mlp_forward",
     "chap_mlp_loss_grad", "chap_mlp_adam", "chap_bs_set_cutoff", "chap_bs_get_cutoff",
-    "chap_bs_move_record", "chap_bs_apply_records",
+    "chap_bs_move_record", "chap_bs_apply_records", "chap_batch_set_persistent", "chap_batch_autotune_mode",
 ]
 
 
@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True):
         "chap_batch_run": (I32, [P, I64, I32, I32, P, P]),
         "chap_batch_autotune": (I32, [P, I32, P]),
         "chap_batch_set_schedule": (I32, [P, I32, I32]),
+        "chap_batch_set_persistent": (I32, [P, I32, I64]),
+        "chap_batch_autotune_mode": (I32, [P, I32, I32, P]),
         "chap_batch_reset": (I32, [P]),
         "chap_batch_get_x": (I32, [P, I32, P]),
         "chap_batch_last_error": (C.c_char_p, [P]),
@@ -476,10 +478,15 @@ class BatchChains:
                                           res, C.byref(secs)))
         return list(res), secs.value
 
-    def autotune(self, iters=5):
-        ch = np.zeros(2, np.int32)
-        self._check(load().chap_batch_autotune(self.h, int(iters), _ptr(ch)))
-        return int(ch[0]), int(ch[1])
+    def autotune(self, iters=5, mode=-1):
+        """(lanes per column, CTAs per SM, persistent) of the fastest schedule
+        (mode 0: three launches per iteration only, 1: persistent only)."""
+        ch = np.zeros(3, np.int32)
+        self._check(load().chap_batch_autotune_mode(self.h, int(iters), int(mode), _ptr(ch)))
+        return int(ch[0]), int(ch[1]), int(ch[2])
+
+    def set_persistent(self, on=True, barrier_limit_ns=0):
+        self._check(load().chap_batch_set_persistent(self.h, 1 if on else 0, int(barrier_limit_ns)))
 
     def set_schedule(self, lanes_per_column, ctas_per_sm):
         self._check(load().chap_batch_set_schedule(self.h, int(lanes_per_column), int(ctas_per_sm)))

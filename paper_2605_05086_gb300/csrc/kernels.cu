@@ -1027,7 +1027,7 @@ __device__ __forceinline__ bool is_candidate(unsigned long long k, unsigned a, u
 //     evaluated again by the whole warp with a list of kWarpSortMax entries.
 
 constexpr int kNbWarps = kEvalWarps;
-constexpr int kQCap = 32 + 4 * 32 - 1;      // queued halves per warp: < 32 left + one round of 4 halves per lane
+constexpr int kQCap = 160;                  // queued halves per warp (more: the whole-warp path)
 using SEnt = SEntry;
 
 // Shape of the group path for G lanes per column: 32 / G columns per warp,
@@ -1123,14 +1123,12 @@ __device__ __forceinline__ void exact_item(const QItem &it, const ColCtx &ci, Ac
     half_case(viol, tight, apos, 0, key, it.w, ci.kl, ci.ku, acc, h);
 }
 
-// Exact pass over n <= 32 queued halves starting at ring position head, one per lane.
+// Exact pass over n <= 32 queued halves starting at queue position head, one per lane.
 template <int G>
 __device__ __noinline__ void flush_queue(NbWarp<G> &W, int head, int n, int lane)
 {
     if (lane < n) {
-        int pos = head + lane;
-        if (pos >= kQCap) pos -= kQCap;
-        const QItem it = W.q[pos];
+        const QItem it = W.q[head + lane];
         const int g = it.meta & 7;
         Acc acc{0, 0, 0, 0};
         Half h;
@@ -1334,33 +1332,24 @@ struct NbLane {
 };
 
 struct NbQueue {
-    int head, qn;
+    int qn;      // queued halves
+    bool ovf;    // the warp's halves did not fit: its columns take the whole-warp path
 };
 
-// Append the lanes' undecided halves to the warp's ring queue.
+// Append the lanes' undecided halves to the warp's queue (exact breakpoints
+// after the classification, 32 at a time); when they do not fit, the warp's
+// columns are evaluated again on the whole-warp path instead.
 template <int G>
 __device__ __forceinline__ void enqueue(NbWarp<G> &W, NbQueue &Q, bool pend, const QItem &it, int lane)
 {
     const unsigned bal = __ballot_sync(FULLMASK, pend);
-    if (pend) {
-        int pos = Q.head + Q.qn + __popc(bal & ((1u << lane) - 1u));
-        if (pos >= kQCap) pos -= kQCap;
-        W.q[pos] = it;
+    const int n = __popc(bal);
+    if (Q.qn + n > kQCap) {
+        Q.ovf = Q.ovf || n > 0;
+        return;
     }
-    Q.qn += __popc(bal);
-}
-
-// Exact pass over 32 queued halves while 32 are queued.
-template <int G>
-__device__ __forceinline__ void drain(NbWarp<G> &W, NbQueue &Q, int lane)
-{
-    __syncwarp();
-    while (Q.qn >= 32) {
-        flush_queue(W, Q.head, 32, lane);
-        Q.head += 32;
-        if (Q.head >= kQCap) Q.head -= kQCap;
-        Q.qn -= 32;
-    }
+    if (pend) W.q[Q.qn + __popc(bal & ((1u << lane) - 1u))] = it;
+    Q.qn += n;
 }
 
 // One half of an integral row (integer variable, exact int64 r and a).  Exact
@@ -1402,7 +1391,6 @@ __device__ __forceinline__ void nb_int_part(const Dev &d, int e0, int n, int nma
         const long long r = row_r(st);
         nb_int_half(r, av, st.z, ok, L, W, Q, acc);
         if (EQ) nb_int_half(-r, -av, st.w, ok, L, W, Q, acc);
-        drain(W, Q, L.lane);
         ok = okn;
         row = rown;
         av = avn;
@@ -1457,7 +1445,6 @@ __device__ __forceinline__ void nb_fp_part(const Dev &d, int e0, int n, int nmax
         const double r = i4_double_lo(s0), m1 = i4_double_lo(s1), m2 = i4_double_hi(s1);
         nb_fp_half(r, a, m1, m2, s0.z, ok, L, W, Q, acc);
         if (EQ) nb_fp_half(dflip(r), dflip(a), m2, m1, s0.w, ok, L, W, Q, acc);
-        drain(W, Q, L.lane);
         ok = okn;
         row = rown;
         a = an;
@@ -1516,7 +1503,7 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
             }
         }
         __syncwarp();
-        NbQueue Q{0, 0};
+        NbQueue Q{0, false};
         Acc acc{0, 0, 0, 0};
         const NbLane L{ilo, ihi, Lp, Ln, Up, Un, tolf, fok, isint, g, lane};
         const int cim = live ? __ldg(d.ci_eq + q0 + cq) : ci0, cfm = live ? __ldg(d.cf_eq + q0 + cq) : cf0;
@@ -1525,8 +1512,9 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
         nb_int_part<G, true>(d, cim, nIe, groups_max<G>(nIe), sub, L, W, Q, acc);
         nb_fp_part<G, false>(d, cf0, nFs, groups_max<G>(nFs), sub, L, W, Q, acc);
         nb_fp_part<G, true>(d, cfm, nFe, groups_max<G>(nFe), sub, L, W, Q, acc);
-        const int head = Q.head, qn = Q.qn;
-        if (qn > 0) flush_queue(W, head, qn, lane);
+        __syncwarp();
+        if (!Q.ovf)
+            for (int h0 = 0; h0 < Q.qn; h0 += 32) flush_queue(W, h0, min(32, Q.qn - h0), lane);
         // group sums of the scalars
 #pragma unroll
         for (int o2 = G >> 1; o2 > 0; o2 >>= 1) {
@@ -1540,7 +1528,7 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_nb(Dev d, int q0, int 
         acc.beta_c += W.beta_c[g];
         acc.alpha_c += W.alpha_c[g];
         const int cnt = W.cnt[g];
-        const bool over = cnt > STG;
+        const bool over = cnt > STG || Q.ovf;
         // Bound: no candidate of the column scores above beta + (its positive
         // deltas) + max(alpha, 0).  A column whose bound is not positive, or
         // is below an admissible score already found in this pass, cannot

@@ -1,6 +1,10 @@
 """Batched tabu chains (chap_batch_*) against the single-handle path and the
 oracle: every chain must follow exactly the trajectory of chap_bs_step on its
-instance with its tenure (same moves, weights, stopping iteration)."""
+instance with its tenure (same moves, weights, stopping iteration), under both
+schedules (three launches per iteration, one persistent launch with grid
+barriers).  A barrier whose wait bound is set to 1 ns runs out: the run
+returns CHAP_E_TIMEOUT, nothing faults, and the batch works again after a
+reset."""
 import numpy as np
 import pytest
 
@@ -44,14 +48,16 @@ def single_run(chap, prob, tenure, iters, stop):
     return r, st
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("schedule", [(8, 4), (4, 2), (16, 8), (2, 4)])
-def test_chains_follow_single_handles(chap, schedule):
+def test_chains_follow_single_handles(chap, schedule, persistent):
     probs = [inst.gen_setcover(seed=5, n=300, m=150, k=6), binary_mixed(7, 500, 260),
              inst.gen_setcover(seed=6, n=1300, m=700, k=8)]
     chain_prob = [0, 0, 1, 1, 2, 2, 1]
     tenures = [3, 10, 3, 10, 5, 20, 0]
     b = chap.BatchChains(probs, chain_prob, tenures)
     b.set_schedule(*schedule)
+    b.set_persistent(persistent)
     res, _ = b.run(max_iters=300, stop_at_feasible=False, graph_iters=32)
     for c, (k, t) in enumerate(zip(chain_prob, tenures)):
         r, st = single_run(chap, probs[k], t, 300, False)
@@ -61,11 +67,13 @@ def test_chains_follow_single_handles(chap, schedule):
     b.close()
 
 
-def test_stop_at_feasible_and_continue(chap):
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_stop_at_feasible_and_continue(chap, persistent):
     probs = [inst.gen_setcover(seed=s, n=400 + 300 * s, m=200 + 150 * s, k=6) for s in range(3)]
     chain_prob = [0, 1, 2, 0, 1, 2]
     tenures = [10, 10, 10, 2, 2, 2]
     b = chap.BatchChains(probs, chain_prob, tenures)
+    b.set_persistent(persistent)
     res, secs = b.run(max_iters=5000, stop_at_feasible=True, graph_iters=64)
     for c, (k, t) in enumerate(zip(chain_prob, tenures)):
         r, st = single_run(chap, probs[k], t, 5000, True)
@@ -103,8 +111,8 @@ def test_autotune_keeps_results(chap):
     b = chap.BatchChains(probs, chain_prob, tenures)
     res_a, _ = b.run(max_iters=200, stop_at_feasible=False)
     xa = [b.x(c) for c in range(len(chain_prob))]
-    g, ctas = b.autotune(iters=3)
-    assert g in (2, 4, 8, 16) and ctas in (2, 4, 8)
+    g, ctas, pers = b.autotune(iters=3)
+    assert g in (2, 4, 8, 16) and ctas in (2, 4, 8) and pers in (0, 1)
     res_b, _ = b.run(max_iters=200, stop_at_feasible=False)
     for c in range(len(chain_prob)):
         assert (res_a[c].moves, res_a[c].final_nviol) == (res_b[c].moves, res_b[c].final_nviol)
@@ -116,3 +124,29 @@ def test_unsupported_instance_rejected(chap):
     prob = inst.gen_tiny_mixed(0, n=6, m=5)
     with pytest.raises(chap.ChapError):
         chap.BatchChains([prob], [0], [3])
+
+
+def test_persistent_barrier_wait_runs_out(chap):
+    """A barrier bound of 1 ns makes the first wait that is not met at once
+    run out: every CTA leaves the launch, the run reports CHAP_E_TIMEOUT, the
+    context stays usable, and after a reset the same batch (default bound)
+    follows the single-handle trajectories again."""
+    probs = [inst.gen_setcover(seed=5, n=3000, m=1500, k=6), binary_mixed(8, 2000, 1000)]
+    chain_prob = [0, 1, 0, 1]
+    tenures = [3, 3, 10, 10]
+    b = chap.BatchChains(probs, chain_prob, tenures)
+    b.set_schedule(8, 4)
+    b.set_persistent(1, barrier_limit_ns=1)
+    with pytest.raises(chap.ChapError) as ei:
+        b.run(max_iters=64, stop_at_feasible=False, graph_iters=16)
+    assert ei.value.status == chap.CHAP_E_TIMEOUT
+    with pytest.raises(chap.ChapError) as ei:
+        b.run(max_iters=8, stop_at_feasible=False)
+    assert ei.value.status == chap.CHAP_E_STATE
+    b.reset()
+    b.set_persistent(1, barrier_limit_ns=2_000_000_000)
+    res, _ = b.run(max_iters=100, stop_at_feasible=False, graph_iters=16)
+    for c, (k, t) in enumerate(zip(chain_prob, tenures)):
+        r, st = single_run(chap, probs[k], t, 100, False)
+        assert res[c].moves == st["moves"] and np.array_equal(b.x(c), st["x"]), c
+    b.close()
