@@ -314,14 +314,26 @@ def run_learned(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream().cuda_stream
-    cap = args.learned_cap
-    train_prob = inst.gen_setcover(seed=21, n=200_000, m=100_000, k=8)
-    prob = inst.make("setcover_200k")
+    general = args.workload == "learned_general"
+    cap = min(args.learned_cap, 60_000) if general else args.learned_cap
+    # training pairs logged by the exact driver from both workload families:
+    # a set cover of 200k variables (another seed) and the general 200k-var MIP
+    # itself (13 + 12 passes: about 5M pairs)
     t0 = time.perf_counter()
-    tb = chap.BestShift(train_prob, stream=stream, tenure=10)
-    x, t = learn.log_pairs(tb, passes=25, iters_between=40)
-    tb.close()
+    xs, ts = [], []
+    for train_prob, passes in ((inst.gen_setcover(seed=21, n=200_000, m=100_000, k=8), 13),
+                               (inst.make("general_200k"), 12)):
+        tb = chap.BestShift(train_prob, stream=stream, tenure=10)
+        x, t = learn.log_pairs(tb, passes=passes, iters_between=40)
+        xs.append(x)
+        ts.append(t)
+        tb.close()
+    x, t = torch.cat(xs), torch.cat(ts)
     t_log = time.perf_counter() - t0
+    # evaluation instance: the set cover of config 5, or a general-family MIP
+    # (config-2 shape, 20k variables: the family does not reach feasibility
+    # within the cap, so the runs are compared at an equal iteration count)
+    prob = inst.gen_general(seed=31, n=20_000, m=10_000, len_cap=60) if general else inst.make("setcover_200k")
     t0 = time.perf_counter()
     wbf, _, curve = learn.train(x, t, epochs=2, batch=8192, lr=2e-3)
     torch.cuda.synchronize()
@@ -338,23 +350,26 @@ def run_learned(args):
     lh.close()
     value = rl.moves / rl.seconds
     line = {
-        "metric": "tabu moves/s, learned proposal (top-k 4096, exact pass every 50), set-cover 200k vars",
+        "metric": ("tabu moves/s, learned proposal (top-k 4096, exact pass every 50), "
+                   + ("general-family MIP 20k vars" if general else "set-cover 200k vars")),
         "value": value, "unit": "moves/s", "n_gpus": 1, "steps": int(rl.iters), "warmup": 0,
         "ms_per_step": rl.seconds * 1e3 / max(1, rl.iters), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 network / int64 exact scores", "data": "synthetic",
-        "config": {"workload": "learned_200k", "n": prob.n, "m": prob.m, "nnz": prob.nnz, "topk": 4096,
+        "config": {"workload": args.workload, "n": prob.n, "m": prob.m, "nnz": prob.nnz, "topk": 4096,
                    "exact_every": 50, "propose_every": args.propose_every, "iteration_cap": cap,
                    "training": {"pairs": int(x.shape[0]), "log_seconds": t_log, "train_seconds": t_train,
                                 "epochs": 2, "batch": 8192, "loss_per_epoch": curve,
-                                "instance": "set cover 200k vars, seed 21"},
+                                "instances": "set cover 200k vars (seed 21, 13 passes) and the general "
+                                             "200k-var MIP (12 passes), 40 iterations apart"},
                    "learned": {"iters": rl.iters, "moves": rl.moves, "seconds": rl.seconds,
                                "feasible_iter": rl.feasible_iter, "time_to_feasible_s": rl.time_to_feasible_s,
                                "exact_passes": rl.exact_passes, "top1_misses": rl.misses,
                                "top1_miss_rate": rl.misses / max(1, rl.exact_passes),
-                               "final_nviol": rl.final_nviol},
+                               "final_nviol": rl.final_nviol, "best_nviol": rl.best_nviol},
                    "plain_exact": {"iters": rp.iters, "moves": rp.moves, "seconds": rp.seconds,
                                    "moves_per_s": rp.moves / rp.seconds, "feasible_iter": rp.feasible_iter,
-                                   "time_to_feasible_s": rp.time_to_feasible_s, "final_nviol": rp.final_nviol}},
+                                   "time_to_feasible_s": rp.time_to_feasible_s, "final_nviol": rp.final_nviol,
+                                   "best_nviol": rp.best_nviol}},
         "e2e": {"value": rl.moves / (rl.seconds + t_log + t_train), "unit": "moves/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                 "call": "pair logging + training + chap_learned_run (instance already on the device)"},
@@ -393,7 +408,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="general_200k", choices=sorted(inst.WORKLOADS) + ["batch_64x4", "learned_200k", "multiclimb_200k"])
+    ap.add_argument("--workload", default="general_200k",
+                    choices=sorted(inst.WORKLOADS) + ["batch_64x4", "learned_200k", "learned_general", "multiclimb_200k"])
     ap.add_argument("--batch-cap", type=int, default=20000, help="iteration cap per chain (batch_64x4)")
     ap.add_argument("--learned-cap", type=int, default=300000, help="iteration cap (learned_200k)")
     ap.add_argument("--propose-every", type=int, default=50, help="iterations between proposals (learned_200k)")
@@ -409,7 +425,7 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "compared against one chain of the same GPU path"}))
             return 0
         return run_multiclimb(args)
-    if args.workload == "learned_200k":
+    if args.workload in ("learned_200k", "learned_general"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the learned path is compared against the GPU "
                               "plain exact driver on the same instance instead"}))

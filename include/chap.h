@@ -157,7 +157,7 @@ typedef struct chap_info {
     int32_t bin_lanes;        /* lanes that score one binary column (2, 4, 8 or 16) */
     int32_t nb_lanes;         /* lanes that score one short non-binary column (4 or 8) */
     int32_t n_long_cols;      /* columns on the multi-CTA merge-sort path (lists over 8192 entries) */
-    int32_t reserved;
+    int32_t n_cta_cols;       /* columns on the one-CTA shared-memory sort path (129..8192 entries) */
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);
@@ -450,8 +450,11 @@ CHAP_API const char *chap_batch_last_error(const struct chap_batch *b);
  *   (device float[n], may be NULL): one training pair per variable.
  * chap_bs_propose: features, predictions (pred: device float[n], may be NULL)
  *   and the k selected variables (list: device int32[k], may be NULL).
- * chap_learned_run: the learned tabu loop from the current state (all-binary
- *   instances); propose_every: iterations between two proposals.
+ * chap_learned_run: the learned tabu loop from the current state;
+ *   propose_every: iterations between two proposals.  Between exact passes
+ *   the proposed binary variables are scored by their flips and the proposed
+ *   non-binary columns with at most 128 breakpoint entries by Algorithm 1
+ *   (exact scores); longer columns are moved only at the exact passes.
  * chap_mlp_forward: y[n] = network(x[n x 12]) (device pointers).
  * chap_mlp_loss_grad: adds the gradient of mean((y - t)^2) over the n rows to
  *   grad[CHAP_MLP_PARAMS] and the sum of squared errors to loss[0] (device).

@@ -86,7 +86,7 @@ class chap_info(C.Structure):
                 ("launches_per_step", C.c_int32), ("grid_bin", C.c_int32), ("grid_nb", C.c_int32),
                 ("bytes_bin", C.c_int64), ("bytes_nb", C.c_int64), ("bytes_cta", C.c_int64),
                 ("bytes_hist", C.c_int64), ("bin_lanes", C.c_int32), ("nb_lanes", C.c_int32),
-                ("n_long_cols", C.c_int32), ("reserved", C.c_int32)]
+                ("n_long_cols", C.c_int32), ("n_cta_cols", C.c_int32)]
 
 
 _lib = None

@@ -701,6 +701,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     in.eval_blocks = n_tb + n_tn + n_tc + (int)tiles_hist.size() + (int)tiles_lscan.size();
     in.n_hist_cols = (int)hcols.size();
     in.n_long_cols = (int)lcols.size();
+    in.n_cta_cols = n_tc;
     // evaluation kernels (they also select the move), a selection kernel only
     // when none runs, the move apply and the weight bump
     in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + (n_bb == 0) + 2 +

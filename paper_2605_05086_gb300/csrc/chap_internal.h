@@ -308,6 +308,10 @@ cudaError_t launch_unpack_r(const Dev &d, double *r_norm, cudaStream_t st);
 cudaError_t launch_tabu_convert(int n, const int *src32, long long *dst64, cudaStream_t st);
 cudaError_t launch_objective(const Dev &d, double *out, cudaStream_t st);  // c^T x into out[0] (device)
 cudaError_t launch_move_record(const Dev &d, chap_move_record *rec, cudaStream_t st);
+// Learned proposal: exact best shift of the short non-binary columns among list[0..k)
+// (whole-warp path), folded into *key with their values in xh (see kernels.cu).
+cudaError_t launch_subset_nb(const Dev &d, const LaunchPlan &p, const int *list, int k, double *xh,
+                             unsigned long long *key, int gate, cudaStream_t st);
 cudaError_t launch_apply_records(const Dev &d, const chap_move_record *recs, int k, cudaStream_t st);
 
 // Sizes used by both sides.

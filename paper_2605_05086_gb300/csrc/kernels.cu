@@ -2069,6 +2069,34 @@ __global__ void __launch_bounds__(kLongThreads) k_long_eval(Dev d, const SEntry 
     finish_pass(d);
 }
 
+// Exact evaluation (Algorithm 1 on the whole-warp path) of the short
+// non-binary columns among the listed variables, for the learned proposal:
+// one warp per listed column; the column's best admissible positive move is
+// folded into *key (score << 22 | (2^22 - 1 - var), 64-bit atomicMax: larger
+// score, then lower variable) and its value written to xh[var].  Binary
+// variables and longer columns in the list are skipped (the flip kernel and
+// the exact passes cover them).
+__global__ void __launch_bounds__(kEvalThreads) k_subset_eval_nb(Dev d, const int *list, int k, int nb_q0, int nb_cols,
+                                                                 double *xh, unsigned long long *key, int gate)
+{
+    if (gated_done(d, gate)) return;
+    __shared__ __align__(16) SEnt stage[kEvalWarps][kWarpSortMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
+    for (int idx = blockIdx.x * kEvalWarps + warp; idx < k; idx += gridDim.x * kEvalWarps) {
+        const int q = d.vpos[list[idx]];
+        if (q < nb_q0 || q >= nb_q0 + nb_cols) continue;   // uniform over the warp
+        Cand best{0, kNoVar, 0, 0.0};
+        const VarOut none{nullptr, nullptr, nullptr};
+        column_warp(d, none, q, stage[warp], iter, nviol, bestnv, best);
+        if (lane == 0 && best.s > 0 && best.var != kNoVar) {
+            xh[best.var] = best.xhat;
+            atomicMax(key, ((unsigned long long)best.s << 22) | (unsigned long long)((1 << 22) - 1 - best.var));
+        }
+        __syncwarp();
+    }
+}
+
 // Default of every per-variable output (fixed variables keep it).
 __global__ void k_fill_outputs(Dev d, VarOut o)
 {
@@ -2796,6 +2824,15 @@ cudaError_t launch_unpack_w(const Dev &d, int *w, cudaStream_t st)
 cudaError_t launch_unpack_r(const Dev &d, double *r, cudaStream_t st)
 {
     k_unpack_r<<<grid_for(d.m, 256), 256, 0, st>>>(d, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_subset_nb(const Dev &d, const LaunchPlan &p, const int *list, int k, double *xh,
+                             unsigned long long *key, int gate, cudaStream_t st)
+{
+    if (p.nb_cols == 0 || k < 1) return cudaSuccess;
+    k_subset_eval_nb<<<grid_for((long long)k * 32, kEvalThreads, 152 * 8), kEvalThreads, 0, st>>>(
+        d, list, k, p.nb_q0, p.nb_cols, xh, key, gate);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,7 @@ struct __align__(16) LearnCtl {
 };
 
 struct Learn {
+    double *xh;                   // value of the best shift of each proposed non-binary column [n]
     float *colviol, *colwv;       // pass-time column features [n]
     long long *s_last;            // exact scores of the last pass [n]
     __nv_bfloat16 *feat;          // [n x 12]
@@ -621,8 +622,9 @@ __global__ void __launch_bounds__(256) k_subset_eval(Dev d, Learn L, int k, int 
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; base < k; base += nwarps * 4) {
         const int idx = base + g;
-        const bool live = idx < k;
-        const int j = live ? L.list[idx] : 0;
+        const int jl = idx < k ? L.list[idx] : 0;
+        const bool live = idx < k && d.vtype[jl] == kVarBin;   // other columns: k_subset_eval_nb
+        const int j = live ? jl : 0;
         const int q = d.vpos[j];
         const bool up = __double_as_longlong(d.x[j]) == 0;
         long long s = 0;
@@ -706,7 +708,7 @@ __global__ void k_learn_select(Dev d, Learn L, int gate)
         c->mv_s = (long long)(key >> kVarBits);
         c->mv_dc = 0;
         c->mv_old = x;
-        c->mv_new = __double_as_longlong(x) == 0 ? 1.0 : 0.0;
+        c->mv_new = d.vtype[j] == kVarBin ? (__double_as_longlong(x) == 0 ? 1.0 : 0.0) : L.xh[j];
     } else {
         c->mv_var = -1;
         c->mv_s = 0;
@@ -807,8 +809,9 @@ chap_status ensure_learn(chap_bs *h, LearnHost **out)
     L.bcnt = lalloc<int>(lh, 2 * (size_t)std::max(1, L.nblocks));
     L.bpre = lalloc<int>(lh, 2 * (size_t)std::max(1, L.nblocks));
     L.list = lalloc<int>(lh, n);
+    L.xh = lalloc<double>(lh, n);
     L.lc = lalloc<LearnCtl>(lh, 1);
-    bool ok = L.colviol && L.colwv && L.s_last && L.feat && L.y && L.hist && L.bcnt && L.bpre && L.list && L.lc &&
+    bool ok = L.colviol && L.colwv && L.s_last && L.feat && L.y && L.hist && L.bcnt && L.bpre && L.list && L.xh && L.lc &&
               cudaMallocHost(&lh->h_lc, sizeof(LearnCtl)) == cudaSuccess;
     cudaError_t e = cudaSuccess;
     if (ok) {
@@ -872,8 +875,11 @@ cudaError_t launch_propose(chap_bs *h, LearnHost *lh, const __nv_bfloat16 *w, in
 
 cudaError_t launch_subset(chap_bs *h, LearnHost *lh, int k, int gate, cudaStream_t st)
 {
-    k_subset_eval<<<grid_n((long long)k * 8, 256, 152 * 4), 256, 0, st>>>(h->dev, lh->L, k, gate);
-    return cudaGetLastError();
+    if (h->info.n_bin > 0) k_subset_eval<<<grid_n((long long)k * 8, 256, 152 * 4), 256, 0, st>>>(h->dev, lh->L, k, gate);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && h->info.n_bin < h->n - h->info.n_fixed)
+        e = launch_subset_nb(h->dev, h->plan, lh->L.list, k, lh->L.xh, &lh->L.lc->key, gate, st);
+    return e;
 }
 
 }  // namespace
@@ -946,8 +952,8 @@ chap_status chap_learned_run(chap_bs *h, const uint16_t *weights, const chap_lea
     if (lo->topk < 1 || lo->exact_every < 1 || lo->propose_every < 1 || lo->max_iters < 0)
         return lfail(h, CHAP_E_INVALID, "bad learned-run options");
     if (own_scratch_ok(h) != CHAP_OK || whole_instance_ok(h) != CHAP_OK) return CHAP_E_STATE;
-    if (h->info.n_bin != h->n - h->info.n_fixed || h->n >= (1 << kVarBits))
-        return lfail(h, CHAP_E_UNSUPPORTED, "the learned driver handles all-binary instances below 2^22 variables");
+    if (h->n >= (1 << kVarBits))
+        return lfail(h, CHAP_E_UNSUPPORTED, "the learned driver handles instances below 2^22 variables");
     LearnHost *lh = nullptr;
     chap_status s = ensure_learn(h, &lh);
     if (s != CHAP_OK) return lfail(h, s, "learned-driver state");

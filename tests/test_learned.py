@@ -175,3 +175,59 @@ def test_tensor_core_forward_in_proposals(env):
     ref16 = np.maximum(h1 @ q["W2"] + q["b2"], 0.0) @ q["w3"] + q["b3"][0]
     assert np.max(np.abs(got - ref16)) <= 1e-4 * max(1.0, np.max(np.abs(ref16))), np.max(np.abs(got - ref16))
     bs.close()
+
+
+def _mixed_small(seed):
+    """General-family instance (binary, integer and continuous variables, integral
+    and N(0,1) rows) with short columns only: every non-binary column is
+    evaluated by the proposal's Algorithm 1 kernel."""
+    return inst.gen_general(seed=seed, n=6000, m=3000, len_cap=40)
+
+
+@pytest.mark.parametrize("mode", ["all_vars", "exact_every_iteration"])
+def test_learned_loop_reduces_to_exact_mixed(env, mode):
+    """Mixed instance: with k = n the proposal evaluates every column exactly
+    (flips and Algorithm 1), so the learned loop takes the plain driver's
+    moves, shift values included."""
+    torch, chap, learn = env
+    prob = _mixed_small(3)
+    w = learn.to_bf16_bits(torch.tensor(learn.init_params(1), device="cuda"))
+    a = chap.BestShift(prob, tenure=5)
+    b = chap.BestShift(prob, tenure=5)
+    assert a.info.n_int > 0 and a.info.n_cont > 0
+    assert a.info.n_cta_cols == 0 and a.info.n_hist_cols == 0 and a.info.n_long_cols == 0
+    kw = dict(topk=prob.n, exact_every=7, propose_every=3) if mode == "all_vars" else \
+        dict(topk=50, exact_every=1, propose_every=1)
+    r = chap.chap_learned_run(a.h, w, max_iters=200, stop_at_feasible=False, **kw)
+    b.run(max_iters=200, stop_at_feasible=0)
+    sa, sb = a.state(), b.state()
+    assert r.iters == 200
+    assert np.array_equal(sa["x"], sb["x"]) and np.array_equal(sa["w"], sb["w"])
+    assert (sa["moves"], sa["nviol"], sa["best_nviol"]) == (sb["moves"], sb["nviol"], sb["best_nviol"])
+    if mode == "all_vars":
+        assert r.misses == 0
+
+
+def test_training_on_both_families_lowers_the_miss_rate_on_mixed(env):
+    """Pairs logged from a set-cover and a general-family instance (the two
+    workloads' families), trained on the GPU: fewer top-1 misses at the exact
+    passes on a mixed instance than the untrained network."""
+    torch, chap, learn = env
+    xs, ts = [], []
+    for prob in (inst.gen_setcover(seed=12, n=20_000, m=10_000, k=8), inst.gen_general(seed=13, n=20_000, m=10_000,
+                                                                                         len_cap=60)):
+        bs = chap.BestShift(prob, tenure=10)
+        x, t = learn.log_pairs(bs, passes=8, iters_between=25)
+        xs.append(x); ts.append(t)
+        bs.close()
+    wbf, _, curve = learn.train(torch.cat(xs), torch.cat(ts), epochs=4, batch=2048, lr=3e-3, seed=0)
+    assert curve[-1] < curve[0]
+    prob = inst.gen_general(seed=14, n=20_000, m=10_000, len_cap=60)
+    rates = {}
+    for name, w in (("trained", wbf), ("untrained", learn.to_bf16_bits(torch.tensor(learn.init_params(0), device="cuda")))):
+        h = chap.BestShift(prob, tenure=10)
+        r = chap.chap_learned_run(h.h, w, topk=512, exact_every=10, propose_every=1, max_iters=400,
+                                  stop_at_feasible=False)
+        rates[name] = r.misses / max(1, r.exact_passes)
+        h.close()
+    assert rates["trained"] < rates["untrained"], rates
