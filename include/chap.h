@@ -103,7 +103,13 @@ typedef struct chap_problem {
  * a new state or a tightened cutoff recomputes all of them.  Tabu and
  * aspiration are applied to the kept values at every iteration, so every
  * result equals the full pass; the non-binary columns are evaluated in full
- * at every iteration either way.
+ * at every iteration either way.  bin_kernel (create time): how the binary
+ * flips are scored in a full pass: column by column (1; a group of lanes per
+ * column gathers its rows' states), row by row (2; Sec. 3.1 "Memory
+ * Considerations", third point: each row state read once for all its binary
+ * entries, the flip terms added into shared-memory column accumulators of a
+ * thread-block cluster), or chosen by the library (0, default: column by
+ * column, measured faster on the workloads here).
  */
 typedef struct chap_options {
     double feas_tol;
@@ -115,7 +121,8 @@ typedef struct chap_options {
     int32_t static_scratch_only; /* create time, default 0: see chap_bs_best_shift_static_scratch */
     int32_t shard_rank;          /* create time: column shard of this handle (see chap_bs_move_record) */
     int32_t shard_count;         /* create time, default 0 or 1: the handle evaluates every column */
-    int32_t reserved[3];
+    int32_t bin_kernel;          /* create time: binary flips 0 automatic, 1 column-wise, 2 row-wise */
+    int32_t reserved[2];
 } chap_options;
 
 /* One move.  var = -1 means "no admissible variable has a positive score": the
@@ -158,6 +165,8 @@ typedef struct chap_info {
     int32_t nb_lanes;         /* lanes that score one short non-binary column (4 or 8) */
     int32_t n_long_cols;      /* columns on the multi-CTA merge-sort path (lists over 8192 entries) */
     int32_t n_cta_cols;       /* columns on the one-CTA shared-memory sort path (129..8192 entries) */
+    int32_t bin_rows;         /* 1: binary flips scored row-wise (clusters over column blocks) */
+    int32_t reserved;
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);

@@ -291,6 +291,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     if (!(h->opt.feas_tol >= 0.0) || h->opt.tenure < 0 || h->opt.graph_iters < 1 ||
         (h->opt.lazy_binary != 0 && h->opt.lazy_binary != 1) ||
         (h->opt.static_scratch_only != 0 && h->opt.static_scratch_only != 1) ||
+        h->opt.bin_kernel < 0 || h->opt.bin_kernel > 2 ||
         h->opt.shard_count < 0 || (h->opt.shard_count > 1 && (h->opt.shard_rank < 0 ||
                                                               h->opt.shard_rank >= h->opt.shard_count))) {
         delete h;
@@ -548,7 +549,75 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         bin_G = (mean <= kBinG2MaxLen && bin_cols >= kBinG2MinCols) ? 2
                 : mean <= kBinG4MaxLen ? 4 : (mean <= kBinG8MaxLen ? 8 : 16);
     }
-    const int n_tb = bin_cols > 0 ? bin_grid_size(bin_cols, bin_G) : 0, n_tc = (int)tiles_cta.size();
+    // row-wise binary flips (k_eval_bin_rows) on request (option bin_kernel:
+    // 0 automatic = column-wise, which measured faster on every workload here;
+    // 1 column-wise; 2 row-wise); the kept scores of lazy_binary stay column-wise
+    const bool lazy_bin = h->opt.lazy_binary != 0 && bin_cols > 0;
+    const bool bin_rows = bin_cols > 0 && !lazy_bin && h->opt.bin_kernel == 2;
+    const int rb_blocks = bin_rows ? (bin_cols + kRbCols - 1) / kRbCols : 0;
+    std::vector<int> rb_rows[2], rb_eptr[2], rb_split[2], rb_vi;
+    std::vector<unsigned short> rb_col[2];
+    std::vector<unsigned char> rb_own[2];
+    std::vector<double> rb_vf;
+    int64_t rb_bytes = 0;
+    if (bin_rows) {
+        // per block and store (0: integral rows, 1: others): the rows with
+        // entries in the block, in order, and their entries
+        struct Part { std::vector<int> rows, eptr; std::vector<unsigned short> col; std::vector<int> vi; std::vector<double> vf; int last = -1; };
+        std::vector<Part> parts(2 * (size_t)rb_blocks);
+        for (int i = 0; i < m; ++i) {
+            const int t = rint[i] ? 0 : 1;
+            for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e) {
+                const int q = vpos[p->col_idx[e]];
+                if (q >= bin_cols) continue;
+                const int b = q % rb_blocks;
+                Part &pt = parts[2 * (size_t)b + t];
+                if (pt.last != i) { pt.last = i; pt.rows.push_back(i); pt.eptr.push_back((int)pt.col.size()); }
+                pt.col.push_back((unsigned short)(q / rb_blocks));
+                if (t == 0) pt.vi.push_back((int)row_val[e]); else pt.vf.push_back(row_val[e]);
+            }
+        }
+        for (int t = 0; t < 2; ++t) {
+            rb_eptr[t].push_back(0);
+            for (int b = 0; b < rb_blocks; ++b) {
+                Part &pt = parts[2 * (size_t)b + t];
+                const int r0 = (int)rb_rows[t].size(), e0 = (int)rb_col[t].size();
+                const int nrow = (int)pt.rows.size(), nent = (int)pt.col.size();
+                rb_rows[t].insert(rb_rows[t].end(), pt.rows.begin(), pt.rows.end());
+                for (int k = 1; k < nrow; ++k) rb_eptr[t].push_back(e0 + pt.eptr[k]);
+                if (nrow) rb_eptr[t].push_back(e0 + nent);
+                rb_col[t].insert(rb_col[t].end(), pt.col.begin(), pt.col.end());
+                if (t == 0) rb_vi.insert(rb_vi.end(), pt.vi.begin(), pt.vi.end());
+                else rb_vf.insert(rb_vf.end(), pt.vf.begin(), pt.vf.end());
+                // the CTAs of the block's cluster split its rows by entries
+                for (int r = 0; r <= kRbCluster; ++r) {
+                    const int64_t want = (int64_t)nent * r / kRbCluster;
+                    int k = 0;
+                    while (k < nrow && (int64_t)pt.eptr[k] < want) ++k;
+                    rb_split[t].push_back(r == kRbCluster ? r0 + nrow : r0 + k);
+                }
+                // each entry's row place inside the 32-row chunk it is processed in
+                // (chunks aligned at the start of every CTA's share)
+                rb_own[t].resize(rb_col[t].size());
+                for (int r = 0; r < kRbCluster; ++r) {
+                    const int s0 = rb_split[t][rb_split[t].size() - (kRbCluster + 1) + r];
+                    const int s1 = rb_split[t][rb_split[t].size() - (kRbCluster + 1) + r + 1];
+                    for (int k = s0; k < s1; ++k)
+                        for (int e = rb_eptr[t][k]; e < rb_eptr[t][k + 1]; ++e)
+                            rb_own[t][e] = (unsigned char)((k - s0) & 31);
+                }
+                rb_bytes += (int64_t)nent * (3 + (t == 0 ? 4 : 8)) + (int64_t)nrow * (8 + (t == 0 ? 16 : 32));
+                std::vector<int>().swap(pt.rows);
+                std::vector<int>().swap(pt.eptr);
+                std::vector<unsigned short>().swap(pt.col);
+                std::vector<int>().swap(pt.vi);
+                std::vector<double>().swap(pt.vf);
+            }
+        }
+        rb_bytes += (int64_t)bin_cols * (4 + 8 + 8);
+    }
+    const int n_tb = bin_rows ? rb_blocks * kRbCluster : (bin_cols > 0 ? bin_grid_size(bin_cols, bin_G) : 0);
+    const int n_tc = (int)tiles_cta.size();
     const int slot_hist = n_tb + n_tn + n_tc;
     for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = slot_hist + (int)q;
     const int slot_long = slot_hist + (int)hcols.size();
@@ -609,6 +678,22 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         d.ltsumc = dalloc<int>(h, long_tiles);
         d.lcand = dalloc<LCand>(h, long_tiles);
     }
+    int *rbr_d[2] = {nullptr, nullptr}, *rbe_d[2] = {nullptr, nullptr}, *rbs_d[2] = {nullptr, nullptr};
+    unsigned short *rbc_d[2] = {nullptr, nullptr};
+    unsigned char *rbo_d[2] = {nullptr, nullptr};
+    int *rbvi_d = nullptr;
+    double *rbvf_d = nullptr;
+    if (bin_rows) {
+        for (int t = 0; t < 2; ++t) {
+            rbr_d[t] = dalloc<int>(h, rb_rows[t].size());
+            rbe_d[t] = dalloc<int>(h, rb_eptr[t].size());
+            rbs_d[t] = dalloc<int>(h, rb_split[t].size());
+            rbc_d[t] = dalloc<unsigned short>(h, rb_col[t].size());
+            rbo_d[t] = dalloc<unsigned char>(h, rb_own[t].size());
+        }
+        rbvi_d = dalloc<int>(h, rb_vi.size());
+        rbvf_d = dalloc<double>(h, rb_vf.size());
+    }
     LongCol *lc_d = dalloc<LongCol>(h, lcols.size());
     Tile *tlg_d = dalloc<Tile>(h, tiles_lgen.size()), *tls_d = dalloc<Tile>(h, tiles_lscan.size());
     d.n_long = (int)lcols.size();
@@ -624,7 +709,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
               d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
               d.hbins && d.hacc && h->t_rec && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu &&
               (!lazy || (d.lz_s && d.lz_dc && d.lz_mark && d.lz_list)) && lc_d && tlg_d && tls_d &&
-              (!has_long || (d.lbuf0 && d.lbuf1 && d.lacc && d.ltsum && d.ltsumc && d.lcand));
+              (!has_long || (d.lbuf0 && d.lbuf1 && d.lacc && d.ltsum && d.ltsumc && d.lcand)) &&
+              (!bin_rows || (rbr_d[0] && rbr_d[1] && rbe_d[0] && rbe_d[1] && rbs_d[0] && rbs_d[1] && rbc_d[0] &&
+                             rbc_d[1] && rbo_d[0] && rbo_d[1] && rbvi_d && rbvf_d));
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
     if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
     for (int k = 0; k < 3 && ok; ++k)
@@ -662,6 +749,12 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     UP(tc_d, tiles_cta.data(), tiles_cta.size());
     UP(th_d, tiles_hist.data(), tiles_hist.size()); UP(hc_d, hcols.data(), hcols.size());
     UP(lc_d, lcols.data(), lcols.size());
+    for (int t = 0; t < 2 && bin_rows; ++t) {
+        UP(rbr_d[t], rb_rows[t].data(), rb_rows[t].size()); UP(rbe_d[t], rb_eptr[t].data(), rb_eptr[t].size());
+        UP(rbs_d[t], rb_split[t].data(), rb_split[t].size()); UP(rbc_d[t], rb_col[t].data(), rb_col[t].size());
+        UP(rbo_d[t], rb_own[t].data(), rb_own[t].size());
+    }
+    if (bin_rows) { UP(rbvi_d, rb_vi.data(), rb_vi.size()); UP(rbvf_d, rb_vf.data(), rb_vf.size()); }
     UP(tlg_d, tiles_lgen.data(), tiles_lgen.size()); UP(tls_d, tiles_lscan.data(), tiles_lscan.size());
 #undef UP
     if (e == cudaSuccess && has_long) e = cudaMemsetAsync(d.lacc, 0, sizeof(HistAcc) * lcols.size(), st);
@@ -676,6 +769,9 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     pl.lazy = lazy ? 1 : 0;
     pl.lazy_mark_blocks = 64;
     pl.bin_cols = bin_cols; pl.n_bin = n_tb; pl.bin_G = bin_G;
+    pl.bin_rows = bin_rows ? 1 : 0;
+    pl.rb = RowBin{rb_blocks, 0, rbr_d[0], rbe_d[0], rbc_d[0], rbo_d[0], rbvi_d, rbr_d[1], rbe_d[1], rbc_d[1],
+                   rbo_d[1], rbvf_d, rbs_d[0], rbs_d[1]};
     pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn; pl.nb_G = nb_G;
     pl.tiles_cta = tc_d; pl.n_cta = n_tc; pl.cta_smem = max_cta_n * 20;
     pl.tiles_hist = th_d; pl.n_hist_tiles = (int)tiles_hist.size(); pl.hist_smem = max_hist_d * (int)sizeof(HBin);
@@ -730,7 +826,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         in.bin_lanes = bin_G;
         in.grid_nb = n_tn;
         in.nb_lanes = nb_G;
-        in.bytes_bin = bin_cols ? kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16) : 0;
+        in.bytes_bin = !bin_cols ? 0 : bin_rows ? rb_bytes : kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16);
+        in.bin_rows = bin_rows ? 1 : 0;
         in.bytes_nb = nb_cols ? kernel_bytes(kind_base[T_NB], kind_base[T_NB + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;
         const int ncta = kind_base[T_NB_CTA + 1] - kind_base[T_NB_CTA];
         const int nhist = kind_base[T_NB_HIST + 1] - kind_base[T_NB_HIST];

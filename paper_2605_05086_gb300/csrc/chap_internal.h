@@ -187,6 +187,31 @@ struct LongCol {
     long long base;       // first entry of the column in the entry buffers
 };
 
+// Row-wise binary flips (Sec. 3.1, "Memory Considerations", third point: the
+// binary columns scored row by row).  The binary positions are dealt round
+// robin into blocks of at most kRbCols columns (position q = c * blocks + b
+// is column c of block b); each block has two CSR stores of its nonzeros, one
+// over the integral rows and one over the others, holding only rows with
+// entries in the block (row id, entry offsets, 16-bit local column,
+// coefficient).  A cluster of kRbCluster CTAs scores one block: each CTA
+// streams a share of the block's rows, reads each row state once for all its
+// entries and adds the penalty changes into shared-memory accumulators of the
+// block's columns; the cluster then sums the CTAs' accumulators through
+// distributed shared memory.
+struct RowBin {
+    int blocks;                       // column blocks (clusters)
+    int pad;
+    const int *rows_i, *eptr_i;       // integral rows: row ids, entry offsets (rows + 1 per store, concatenated)
+    const unsigned short *col_i;
+    const unsigned char *own_i;       // per entry: its row's place in the row's aligned chunk of 32 rows
+    const int *val_i;
+    const int *rows_f, *eptr_f;       // other rows
+    const unsigned short *col_f;
+    const unsigned char *own_f;
+    const double *val_f;
+    const int *split_i, *split_f;     // per block: kRbCluster + 1 row-list boundaries of the CTAs
+};
+
 struct Dev {
     int n, m;
     int tenure;
@@ -272,6 +297,8 @@ struct LaunchPlan {
     long long long_entries;    // entries of all long lists (merge grid)
     int slot_nb, slot_cta;     // first block_best slot of each kernel
     int lazy;                  // binary flips through the kept scores (k_eval_bin_lazy, k_bin_scan)
+    int bin_rows;              // binary flips row-wise (k_eval_bin_rows, n_bin = blocks * kRbCluster CTAs)
+    RowBin rb;
     int lazy_mark_blocks;      // CTAs of the marking kernel
     int apply_blocks;          // CTAs of the weight bump
     int apply_move_blocks;     // CTAs of the move apply (longest column / kApplyMoveThreads)
@@ -321,6 +348,9 @@ constexpr int kCtaThreads = 512;
 constexpr int kHistMaxDomain = 4096;    // largest integer domain of the multi-CTA counting sort
 constexpr int kHistChunk = 16384;       // matrix entries per counting-sort CTA
 constexpr int kHistThreads = 512;
+constexpr int kRbCols = 8192;          // binary columns of one row-wise block
+constexpr int kRbCluster = 8;          // CTAs per block (one thread-block cluster)
+constexpr int kRbThreads = 1024;
 constexpr int kLongChunk = 1020;       // nonzeros per generating CTA: <= 4 entries each, + 2 bounds
 constexpr int kLongRun = 4096;         // entries of one sorted run (power of two)
 constexpr int kLongThreads = 512;

@@ -37,6 +37,8 @@
 // order-preserving integer keys.  Scores are int64 half-weight counts.
 #include "chap_internal.h"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -570,6 +572,149 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_bin(Dev d, int ncols, Var
         d.block_best[blockIdx.x] = b;
         if (b.s > 0) atomicMax(&d.ctl->pass_best, b.s);
     }
+    finish_pass(d);
+}
+
+// ------------------------------------------------ row-wise binary flips
+//
+// k_eval_bin_rows: one thread-block cluster per block of binary columns (see
+// RowBin).  Every warp takes 32 rows of its CTA's share at a time: each lane
+// loads one row (id, entry range, row state) and the rows' entries are then
+// scored 32 at a time in order, each lane finding the row of its entry by a
+// binary search over the lanes' entry prefix and reading that row's state
+// from the lane that holds it (no per-entry gather).  The flip's penalty
+// change (the same terms as the column kernel) goes into the CTA's
+// shared-memory accumulators of the block's columns; after a cluster barrier
+// every CTA sums its share of the columns over the cluster's CTAs (distributed
+// shared memory), applies tabu and aspiration and reduces to its candidate.
+
+template <bool FP>
+__device__ __forceinline__ void rb_rows_chunk(const Dev &d, const int *rows, const int *eptr,
+                                              const unsigned short *cols, const unsigned char *own, const void *vals,
+                                              int k0, int k1, const unsigned *xb, int4 *wrow, long long *sacc,
+                                              int *cacc)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = k0 + lane;
+    const bool ok = k < k1;
+    // this chunk's entries: from the first row's start to the last row's end
+    const int ebase = __ldg(eptr + k0);
+    const int eend = __ldg(eptr + min(k0 + 32, k1));
+    if (ok) {
+        const int4 *p = reinterpret_cast<const int4 *>(d.rs + __ldg(rows + k));
+        wrow[2 * lane] = __ldg(p);
+        if (FP) wrow[2 * lane + 1] = __ldg(p + 1);
+    }
+    __syncwarp();
+    for (int e = ebase + lane; e < eend; e += 32) {
+        const int c = __ldg(cols + e);
+        const int o = __ldg(own + e);   // lane (row) of the entry inside the chunk
+        const int4 r0 = wrow[2 * o];
+        const bool up = ((xb[c >> 5] >> (c & 31)) & 1u) == 0;
+        long long sc = 0;
+        int dc = 0;
+        if (!FP) {
+            const int a = __ldg(reinterpret_cast<const int *>(vals) + e);
+            if (r0.w >= 0) flip_int<true>(r0, a, up, sc, dc);
+            else flip_int<false>(r0, a, up, sc, dc);
+        } else {
+            const int4 r1 = wrow[2 * o + 1];
+            const double a = __ldg(reinterpret_cast<const double *>(vals) + e);
+            if (r0.w >= 0) flip_fp<true>(r0, r1, a, up, sc, dc);
+            else flip_fp<false>(r0, r1, a, up, sc, dc);
+        }
+        if (sc) atomicAdd(reinterpret_cast<unsigned long long *>(sacc + c), (unsigned long long)sc);
+        if (dc) atomicAdd(cacc + c, dc);
+    }
+    __syncwarp();
+}
+
+// shared memory of k_eval_bin_rows: column accumulators (score, count), the x
+// bits and every warp's 32 row states
+constexpr int kRbSmem = kRbCols * (int)(sizeof(long long) + sizeof(int)) + kRbCols / 8 +
+                        (kRbThreads / 32) * 64 * (int)sizeof(int4);
+
+__global__ void __launch_bounds__(kRbThreads) k_eval_bin_rows(Dev d, RowBin rb, int bin_cols, VarOut o, int gate)
+{
+    if (gated_done(d, gate)) return;   // the same for every CTA of the grid
+    extern __shared__ __align__(16) unsigned char rb_smem[];
+    long long *sacc = reinterpret_cast<long long *>(rb_smem);
+    int *cacc = reinterpret_cast<int *>(sacc + kRbCols);
+    unsigned *xb = reinterpret_cast<unsigned *>(cacc + kRbCols);
+    int4 *wrows = reinterpret_cast<int4 *>(xb + kRbCols / 32);
+    __shared__ int s_next[2];
+    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int B = rb.blocks, b = blockIdx.x / kRbCluster;
+    const int ncols = (bin_cols - b + B - 1) / B;   // column c of block b is position c * B + b
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        sacc[c] = 0;
+        cacc[c] = 0;
+    }
+    if (threadIdx.x < 2) s_next[threadIdx.x] = 0;
+    for (int c0 = warp * 32; c0 < ncols; c0 += nwarps * 32) {
+        const int c = c0 + lane;
+        bool bit = false;
+        if (c < ncols) bit = __double_as_longlong(d.x[__ldg(d.var_list + c * B + b)]) != 0;
+        const unsigned w = __ballot_sync(FULLMASK, bit);
+        if (lane == 0) xb[c0 >> 5] = w;
+    }
+    __syncthreads();
+    // chunks of 32 rows taken dynamically by the warps (row lengths vary)
+    int4 *wrow = wrows + warp * 64;
+    {
+        const int r0 = __ldg(rb.split_i + b * (kRbCluster + 1) + rank), r1 = __ldg(rb.split_i + b * (kRbCluster + 1) + rank + 1);
+        for (;;) {
+            int ch = 0;
+            if (lane == 0) ch = atomicAdd(&s_next[0], 1);
+            const int k0 = r0 + 32 * __shfl_sync(FULLMASK, ch, 0);
+            if (k0 >= r1) break;
+            rb_rows_chunk<false>(d, rb.rows_i, rb.eptr_i, rb.col_i, rb.own_i, rb.val_i, k0, r1, xb, wrow, sacc, cacc);
+        }
+    }
+    {
+        const int r0 = __ldg(rb.split_f + b * (kRbCluster + 1) + rank), r1 = __ldg(rb.split_f + b * (kRbCluster + 1) + rank + 1);
+        for (;;) {
+            int ch = 0;
+            if (lane == 0) ch = atomicAdd(&s_next[1], 1);
+            const int k0 = r0 + 32 * __shfl_sync(FULLMASK, ch, 0);
+            if (k0 >= r1) break;
+            rb_rows_chunk<true>(d, rb.rows_f, rb.eptr_f, rb.col_f, rb.own_f, rb.val_f, k0, r1, xb, wrow, sacc, cacc);
+        }
+    }
+    cluster.sync();   // every CTA's accumulators are complete
+    const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
+    const int per = (ncols + kRbCluster - 1) / kRbCluster;
+    const int c0 = rank * per, c1 = min(ncols, c0 + per);
+    Cand best{0, kNoVar, 0, 0.0};
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        long long s = 0;
+        int dc = 0;
+#pragma unroll
+        for (int k = 0; k < kRbCluster; ++k) {
+            s += cluster.map_shared_rank(sacc, k)[c];
+            dc += cluster.map_shared_rank(cacc, k)[c];
+        }
+        const int j = __ldg(d.var_list + c * B + b);
+        const bool up = ((xb[c >> 5] >> (c & 31)) & 1u) == 0;
+        bool mv = s > 0;
+        if (mv) {
+            const int stamp = up ? d.tabu_inc[j] : d.tabu_dec[j];
+            mv = iter >= (long long)stamp || nviol + (long long)dc < bestnv;
+        }
+        const double xh = up ? 1.0 : 0.0;
+        if (o.xhat) o.xhat[j] = mv ? xh : d.x[j];
+        if (o.s) o.s[j] = mv ? s : 0;
+        if (o.dc) o.dc[j] = mv ? dc : 0;
+        if (mv && cand_better(s, j, best.s, best.var)) best = Cand{s, j, dc, xh};
+    }
+    const Cand bb = block_reduce_cand(best);
+    if (threadIdx.x == 0) {
+        d.block_best[blockIdx.x] = bb;
+        if (bb.s > 0) atomicMax(&d.ctl->pass_best, bb.s);
+    }
+    cluster.sync();   // the other CTAs are done reading this CTA's accumulators
     finish_pass(d);
 }
 
@@ -2669,6 +2814,7 @@ cudaError_t setup_kernel_attributes(const LaunchPlan &p)
     if (e == cudaSuccess && p.cta_smem > 0) e = raise_smem_limit((const void *)k_eval_cta, 2, p.cta_smem);
     if (e == cudaSuccess && p.hist_smem > 0) e = raise_smem_limit((const void *)k_eval_hist, 3, p.hist_smem);
     if (e == cudaSuccess && p.n_lgen > 0) e = raise_smem_limit((const void *)k_long_gen, 4, long_gen_smem());
+    if (e == cudaSuccess && p.bin_rows) e = raise_smem_limit((const void *)k_eval_bin_rows, 5, kRbSmem);
     return e;
 }
 
@@ -2691,6 +2837,24 @@ static cudaError_t launch_long(const Dev &d, const LaunchPlan &p, const VarOut &
     k_long_tilesum<<<p.n_lscan, kLongThreads, 0, st>>>(d, in, p.tiles_lscan, gate);
     k_long_eval<<<p.n_lscan, kLongThreads, 0, st>>>(d, in, p.tiles_lscan, o, gate);
     return cudaGetLastError();
+}
+
+// The row-wise binary kernel: blocks x kRbCluster CTAs in clusters of kRbCluster.
+static cudaError_t launch_bin_rows(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kRbCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p.rb.blocks * kRbCluster);
+    cfg.blockDim = dim3(kRbThreads);
+    cfg.dynamicSmemBytes = kRbSmem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_eval_bin_rows, d, p.rb, p.bin_cols, o, gate);
 }
 
 cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o, int gate, cudaStream_t st)
@@ -2716,6 +2880,10 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
         default: k_eval_bin_lazy<8><<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, gate); break;
         }
         k_bin_scan<<<p.n_bin, kEvalThreads, 0, st>>>(d, p.bin_cols, o, gate);
+        PROF(0, 1);
+    } else if (p.n_bin && p.bin_rows) {
+        PROF(0, 0);
+        if (e == cudaSuccess) e = launch_bin_rows(d, p, o, gate, st);
         PROF(0, 1);
     } else if (p.n_bin) {
         PROF(0, 0);
