@@ -377,7 +377,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         int64_t E = (std::isfinite(h->lb[j]) ? 1 : 0) + (std::isfinite(h->ub[j]) ? 1 : 0);
         for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) E += (h->row_eq[p->row_idx[e]] ? 2 : 1) * per_half;
         int k;
-        if (E <= kWarpSortMax) k = T_NB;
+        if (E <= (t == CHAP_VAR_CONT ? kWarpListMax : kWarpSortMax)) k = T_NB;
         else if (t == CHAP_VAR_INT && dom <= kHistMaxDomain) k = T_NB_HIST;
         else if (E <= kCtaMaxEntries) k = T_NB_CTA;
         else k = T_NB_LONG;

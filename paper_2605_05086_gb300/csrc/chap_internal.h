@@ -360,7 +360,8 @@ constexpr int kStaticHistCols = 256;      // and columns
 constexpr int kApplyThreads = 256;
 constexpr int kApplyMoveThreads = 1024;
 constexpr int kLazyMaxRows = 2048;      // longer moved columns re-evaluate every kept binary score
-constexpr int kWarpSortMax = 128;       // longest list sorted by one warp (K <= 4)
+constexpr int kWarpSortMax = 128;       // longest list of an integer short column (one warp sorts it, K <= 4)
+constexpr int kWarpListMax = 256;       // ... of a continuous short column (a delta and a marker per half, K <= 8)
 constexpr double kBinG2MaxLen = 6.0;    // mean binary column length up to which 2 lanes score a column
 constexpr int kBinG2MinCols = 32768;    // (and only with this many binary columns: small instances are latency-bound)
 constexpr double kBinG4MaxLen = 16.0;   // ... up to which 4 lanes do

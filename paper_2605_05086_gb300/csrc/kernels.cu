@@ -1197,12 +1197,15 @@ struct __align__(16) QItem {
 
 template <int G>
 struct __align__(16) NbWarp {
-    SEnt stage[kWarpSortMax];               // the groups' lists, or the whole-warp list
-    QItem q[kQCap];                         // ring buffer
+    SEnt stage[kWarpSortMax];               // the groups' lists, or (with q) the whole-warp list
+    QItem q[kQCap];                         // queued halves; free again when the whole-warp path runs
     ColCtx ctx[32 / G];
     long long beta[32 / G], alpha[32 / G];
     int beta_c[32 / G], alpha_c[32 / G], cnt[32 / G];
 };
+// The whole-warp path lays its list over stage and q (kWarpListMax entries).
+static_assert(sizeof(SEnt) * kWarpSortMax + sizeof(QItem) * kQCap >= sizeof(SEnt) * kWarpListMax,
+              "the whole-warp list fits over the stage and the queue");
 // dynamic shared memory of k_eval_nb<G>
 template <int G>
 constexpr int nb_smem() { return kNbWarps * (int)sizeof(NbWarp<G>); }
@@ -1424,8 +1427,9 @@ __device__ __forceinline__ VCand group_sort_scan(const ColCtx &c, const Acc &a, 
     return vb;
 }
 
-// Whole-warp evaluation of one column with up to kWarpSortMax list entries
-// (columns whose list outgrew the group path).  Exact breakpoints inline.
+// Whole-warp evaluation of one column with up to kWarpListMax list entries
+// (columns whose list outgrew the group path; stage holds that many).  Exact
+// breakpoints inline.
 __device__ __noinline__ void column_warp(const Dev &d, const VarOut &o, int q, SEnt *stage, long long iter,
                                          long long nviol, long long bestnv, Cand &best)
 {
@@ -1463,7 +1467,8 @@ __device__ __noinline__ void column_warp(const Dev &d, const VarOut &o, int q, S
     VCand vb;
     if (cnt <= 32) vb = group_sort_scan<1, 32>(c, acc, stage, cnt, nviol, bestnv);
     else if (cnt <= 64) vb = group_sort_scan<2, 32>(c, acc, stage, cnt, nviol, bestnv);
-    else vb = group_sort_scan<4, 32>(c, acc, stage, cnt, nviol, bestnv);
+    else if (cnt <= 128) vb = group_sort_scan<4, 32>(c, acc, stage, cnt, nviol, bestnv);
+    else vb = group_sort_scan<8, 32>(c, acc, stage, cnt, nviol, bestnv);
     if (lane == 0) finish_column(d, o, c, vb, best);
     __syncwarp();
 }
@@ -2225,7 +2230,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_subset_eval_nb(Dev d, const in
                                                                  double *xh, unsigned long long *key, int gate)
 {
     if (gated_done(d, gate)) return;
-    __shared__ __align__(16) SEnt stage[kEvalWarps][kWarpSortMax];
+    __shared__ __align__(16) SEnt stage[kEvalWarps][kWarpListMax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
     for (int idx = blockIdx.x * kEvalWarps + warp; idx < k; idx += gridDim.x * kEvalWarps) {

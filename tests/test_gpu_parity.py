@@ -374,3 +374,40 @@ def test_pass_without_outputs_selects_the_full_pass_move(chap, general_small, wh
             (full.var, full.score_half, full.dnviol, full.new_value), it
         bs.run(max_iters=25, stop_at_feasible=0)
     bs.close()
+
+
+def _continuous_columns(seed, lengths, dom=64, eq_frac=0.2):
+    """Continuous columns j with lengths[j] single-variable rows each (dyadic
+    coefficients, breakpoints inside [0, dom]): a delta and a tight-point marker
+    per half, so lists of up to about 2 * lengths[j] entries."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals, rhs, sense = [], [], [], [], []
+    i = 0
+    for j, L in enumerate(lengths):
+        for _ in range(L):
+            a = float(rng.choice([1, 2, 0.5, -1, -2, -0.5]))
+            t = float(rng.integers(0, 4 * dom + 1)) / 4
+            rows.append(i); cols.append(j); vals.append(a)
+            rhs.append(a * t + float(rng.integers(-1, 2)) * 0.25)
+            sense.append(int(rng.choice([0, 1, 2], p=[(1 - eq_frac) / 2, (1 - eq_frac) / 2, eq_frac])))
+            i += 1
+    n, m = len(lengths), i
+    return inst.from_triplets(f"cont_columns_{seed}", n, m, rows, cols, vals, np.zeros(n), np.full(n, float(dom)),
+                              np.ones(n), np.array(rhs), np.full(n, inst.VAR_CONT), np.array(sense, dtype=np.uint8),
+                              x0=np.zeros(n))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_continuous_lists_whole_warp(chap, seed):
+    """Continuous columns whose lists pass 128 entries (up to 256) stay on the
+    short-column kernel: groups, then the whole-warp path over the warp's
+    stage and queue memory (8 entries per lane); bit-exact on dyadic data."""
+    lengths = [3, 20, 50, 70, 80, 90, 95, 40, 8, 64, 75]
+    prob = _continuous_columns(seed, lengths, eq_frac=0.1)
+    orc = Oracle(prob, feas_tol=0.0)
+    bs = chap.BestShift(prob, tenure=3, feas_tol=0.0)
+    assert bs.info.n_cta_cols == 0 and bs.info.n_long_cols == 0
+    for it in range(4):
+        st = bs.state()
+        assert_exact(bs.best_shift()[:3], oracle_pass(orc, st))
+        bs.run(max_iters=5, stop_at_feasible=0)
