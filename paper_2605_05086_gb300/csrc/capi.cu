@@ -698,6 +698,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     Tile *tlg_d = dalloc<Tile>(h, tiles_lgen.size()), *tls_d = dalloc<Tile>(h, tiles_lscan.size());
     d.n_long = (int)lcols.size();
     h->t_rec = dalloc<chap_move_record>(h, kMaxRecords);
+    h->t_obj = dalloc<double>(h, 1 + 128);
     h->t_xhat = dalloc<double>(h, n);
     h->t_s = dalloc<long long>(h, n);
     h->t_dc = dalloc<int>(h, n);
@@ -707,7 +708,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && ci_eq_d && cf_eq_d && row_ptr_d && col_idx_d &&
               row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.x_best && d.rs &&
               d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
-              d.hbins && d.hacc && h->t_rec && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu &&
+              d.hbins && d.hacc && h->t_rec && h->t_obj && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu &&
               (!lazy || (d.lz_s && d.lz_dc && d.lz_mark && d.lz_list)) && lc_d && tlg_d && tls_d &&
               (!has_long || (d.lbuf0 && d.lbuf1 && d.lacc && d.ltsum && d.ltsumc && d.lcand)) &&
               (!bin_rows || (rbr_d[0] && rbr_d[1] && rbe_d[0] && rbe_d[1] && rbs_d[0] && rbs_d[1] && rbc_d[0] &&
@@ -1210,8 +1211,8 @@ chap_status chap_tabu_run(chap_bs *h, const chap_options *opts, chap_tabu_result
     // c^T x reduced on the device; only the value crosses to the host
     double obj = 0.0;
     if (h->n) {
-        CK(h, launch_objective(d, h->t_xhat, h->st), "objective");
-        CK(h, cudaMemcpyAsync(&obj, h->t_xhat, sizeof(double), cudaMemcpyDeviceToHost, h->st), "copy objective");
+        CK(h, launch_objective(d, h->t_obj, h->t_obj + 1, h->st), "objective");
+        CK(h, cudaMemcpyAsync(&obj, h->t_obj, sizeof(double), cudaMemcpyDeviceToHost, h->st), "copy objective");
         CK(h, cudaStreamSynchronize(h->st), "synchronise");
     }
     res->objective = obj;

@@ -36,6 +36,7 @@ struct chap_bs {
     bool broken = false;
     bool prof_valid = false;   // a pass ran with kernel timing since it was enabled
     chap_move_record *t_rec = nullptr;  // move records staged from host memory
+    double *t_obj = nullptr;            // objective value and the partial sums of its reduction (1 + 128)
     int shard_rank = 0, shard_count = 1;  // column shard evaluated by this handle
     int64_t hist_bins = 0;     // counting-sort bins of the instance
     bool no_hist_scratch = false; // created without the counting-sort scratch (static_scratch_only)

@@ -333,7 +333,8 @@ cudaError_t launch_lazy_init(const Dev &d, cudaStream_t st);
 cudaError_t launch_unpack_w(const Dev &d, int *w_norm, cudaStream_t st);
 cudaError_t launch_unpack_r(const Dev &d, double *r_norm, cudaStream_t st);
 cudaError_t launch_tabu_convert(int n, const int *src32, long long *dst64, cudaStream_t st);
-cudaError_t launch_objective(const Dev &d, double *out, cudaStream_t st);  // c^T x into out[0] (device)
+// c^T x into out[0] (device); partial: device scratch of 128 doubles (kObjBlocks)
+cudaError_t launch_objective(const Dev &d, double *out, double *partial, cudaStream_t st);
 cudaError_t launch_move_record(const Dev &d, chap_move_record *rec, cudaStream_t st);
 // Learned proposal: exact best shift of the short non-binary columns among list[0..k)
 // (whole-warp path), folded into *key with their values in xh (see kernels.cu).

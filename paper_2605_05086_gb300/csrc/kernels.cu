@@ -2678,21 +2678,40 @@ __global__ void k_unpack_r(Dev d, double *r)
     }
 }
 
-// Objective c^T x of the current assignment into *out: one CTA, a strided
-// partial sum per thread and a fixed reduction tree (the same value on every
-// call for the same x).
-__global__ void __launch_bounds__(1024) k_objective(Dev d, double *out)
+// Objective c^T x of the current assignment: every CTA sums a contiguous chunk
+// of the variables (strided per thread, then a fixed tree), and one CTA adds
+// the partial sums in CTA order: the same value on every call for the same x.
+constexpr int kObjBlocks = 128, kObjThreads = 256;
+
+__device__ __forceinline__ double block_sum_fixed(double s, double *part)
 {
-    __shared__ double part[1024];
-    double s = 0.0;
-    for (int j = threadIdx.x; j < d.n; j += blockDim.x) s = __dadd_rn(s, __dmul_rn(d.obj[j], d.x[j]));
     part[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) part[threadIdx.x] = __dadd_rn(part[threadIdx.x], part[threadIdx.x + o]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = part[0];
+    return part[0];
+}
+
+__global__ void __launch_bounds__(kObjThreads) k_objective_part(Dev d, double *partial)
+{
+    __shared__ double part[kObjThreads];
+    const int per = (d.n + gridDim.x - 1) / gridDim.x;
+    const int j0 = blockIdx.x * per, j1 = min(d.n, j0 + per);
+    double s = 0.0;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) s = __dadd_rn(s, __dmul_rn(d.obj[j], d.x[j]));
+    const double t = block_sum_fixed(s, part);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kObjThreads) k_objective_final(const double *partial, int np, double *out)
+{
+    __shared__ double part[kObjThreads];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) s = __dadd_rn(s, partial[k]);
+    const double t = block_sum_fixed(s, part);
+    if (threadIdx.x == 0) *out = t;
 }
 
 __global__ void k_widen(int n, const int *a, long long *b)
@@ -3021,9 +3040,10 @@ cudaError_t launch_apply_records(const Dev &d, const chap_move_record *recs, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_objective(const Dev &d, double *out, cudaStream_t st)
+cudaError_t launch_objective(const Dev &d, double *out, double *partial, cudaStream_t st)
 {
-    k_objective<<<1, 1024, 0, st>>>(d, out);
+    k_objective_part<<<kObjBlocks, kObjThreads, 0, st>>>(d, partial);
+    k_objective_final<<<1, kObjThreads, 0, st>>>(partial, kObjBlocks, out);
     return cudaGetLastError();
 }
 

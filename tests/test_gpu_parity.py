@@ -411,3 +411,21 @@ def test_continuous_lists_whole_warp(chap, seed):
         st = bs.state()
         assert_exact(bs.best_shift()[:3], oracle_pass(orc, st))
         bs.run(max_iters=5, stop_at_feasible=0)
+
+
+@pytest.mark.parametrize("which", ["setcover", "general"])
+def test_run_objective_reduced_on_device(chap, which):
+    """chap_tabu_run reports c^T x of the state it leaves, reduced on the device:
+    exact on integer data, within the summation-order rounding otherwise."""
+    prob = (inst.gen_setcover(seed=2, n=3000, m=1500, k=8) if which == "setcover"
+            else inst.gen_general(seed=2, n=5000, m=2500, len_cap=60))
+    bs = chap.BestShift(prob, tenure=5)
+    for _ in range(3):
+        r = bs.run(max_iters=40, stop_at_feasible=0)
+        x = bs.state()["x"]
+        want = float(np.dot(prob.obj, x))
+        if which == "setcover":
+            assert r.objective == want
+        else:
+            assert abs(r.objective - want) <= 1e-12 * max(1.0, float(np.abs(prob.obj) @ np.abs(x)))
+    bs.close()
