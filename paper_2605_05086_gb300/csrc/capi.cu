@@ -165,26 +165,23 @@ chap_status check_x(chap_bs *h, const double *x)
     return CHAP_OK;
 }
 
-// Load x (host array) and normalised weights (host array, NULL = 1), recompute residuals.
+// Load x (host array) and normalised weights (host array, NULL = 1), recompute
+// residuals.  x and w go to the device as they are (x canonicalised there);
+// the row states are built on the device from the uploaded weights.
 chap_status load_state(chap_bs *h, const double *x, const int *w, const int *tabu_inc, const int *tabu_dec,
                        long long iter, long long best_nviol, int use_best)
 {
     if (h->broken) return fail(h, CHAP_E_STATE, "handle unusable after a CUDA fault");
     chap_status s = check_x(h, x);
     if (s != CHAP_OK) return s;
-    std::vector<double> xc(x, x + h->n);
-    for (double &v : xc) v = v + 0.0;
-    std::vector<RowState> rs(h->m);
-    for (int i = 0; i < h->m; ++i) {
-        int k = h->nrow_base[i];
-        int w1 = w ? w[k] : 1;
-        int w2 = h->row_eq[i] ? (w ? w[k + 1] : 1) : -1;
-        if (w1 < 1 || (h->row_eq[i] && w2 < 1)) return fail(h, CHAP_E_INVALID, "weights must be >= 1");
-        rs[i] = RowState{0, w1, w2, 0.0, 0.0};
-    }
+    if (w)
+        for (int i = 0; i < h->m; ++i) {
+            const int k = h->nrow_base[i];
+            if (w[k] < 1 || (h->row_eq[i] && w[k + 1] < 1)) return fail(h, CHAP_E_INVALID, "weights must be >= 1");
+        }
     Dev &d = h->dev;
-    CK(h, h2d(d.x, xc.data(), h->n, h->st), "copy x");
-    CK(h, h2d(d.rs, rs.data(), h->m, h->st), "copy weights");
+    CK(h, h2d(d.x, x, h->n, h->st), "copy x");
+    if (w) CK(h, h2d(h->t_w, w, h->m_norm, h->st), "copy weights");
     if (tabu_inc) {
         CK(h, h2d(d.tabu_inc, tabu_inc, h->n, h->st), "copy tabu");
         CK(h, h2d(d.tabu_dec, tabu_dec, h->n, h->st), "copy tabu");
@@ -193,9 +190,9 @@ chap_status load_state(chap_bs *h, const double *x, const int *w, const int *tab
         CK(h, cudaMemsetAsync(d.tabu_dec, 0, sizeof(int) * (size_t)std::max(h->n, 1), h->st), "reset tabu");
     }
     CK(h, cudaMemsetAsync(&d.ctl->nviol, 0, sizeof(long long), h->st), "reset nviol");
-    if (h->m > 0) CK(h, launch_residuals(d, h->st), "residual kernel");
+    CK(h, launch_residuals(d, w ? h->t_w : nullptr, h->st), "residual kernel");
     CK(h, launch_finish_set_state(d, iter, best_nviol, use_best, h->st), "finish set_state");
-    // the host arrays above are released on return: make sure the copies are done
+    // the caller may reuse (or free) its host arrays on return: wait for the copies
     CK(h, cudaStreamSynchronize(h->st), "synchronise");
     return CHAP_OK;
 }
@@ -344,6 +341,19 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         else ++m_fp;
     }
     h->m_norm = mn;
+
+    // rows of the residual kernel: the integral ones in index order, then the
+    // others by decreasing length (32 rows of like length per CTA)
+    std::vector<int> res_rows;
+    res_rows.reserve(m);
+    for (int i = 0; i < m; ++i)
+        if (rint[i]) res_rows.push_back(i);
+    const int n_res_int = (int)res_rows.size();
+    for (int i = 0; i < m; ++i)
+        if (!rint[i]) res_rows.push_back(i);
+    std::stable_sort(res_rows.begin() + n_res_int, res_rows.end(), [&](int a, int b) {
+        return p->row_ptr[a + 1] - p->row_ptr[a] > p->row_ptr[b + 1] - p->row_ptr[b];
+    });
 
     std::vector<double> row_val(p->nnz);
     for (int i = 0; i < m; ++i)
@@ -641,6 +651,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     double *row_val_d = dalloc<double>(h, p->nnz), *rhs_d = dalloc<double>(h, m), *eps_d = dalloc<double>(h, m);
     unsigned char *rint_d = dalloc<unsigned char>(h, m);
     int *nrb_d = dalloc<int>(h, m);
+    int *resr_d = dalloc<int>(h, m);
     unsigned char *vt_d = dalloc<unsigned char>(h, n);
     double *lb_d = dalloc<double>(h, n), *ub_d = dalloc<double>(h, n), *obj_d = dalloc<double>(h, n);
     d.x = dalloc<double>(h, n);
@@ -706,7 +717,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     h->t_r = dalloc<double>(h, mn);
     h->t_tabu = dalloc<long long>(h, n);
     bool ok = ci_ptr_d && ci_row_d && ci_val_d && cf_ptr_d && cf_row_d && cf_val_d && ci_eq_d && cf_eq_d && row_ptr_d && col_idx_d &&
-              row_val_d && rhs_d && eps_d && rint_d && nrb_d && vt_d && lb_d && ub_d && obj_d && d.x && d.x_best && d.rs &&
+              row_val_d && rhs_d && eps_d && rint_d && nrb_d && resr_d && vt_d && lb_d && ub_d && obj_d && d.x && d.x_best && d.rs &&
               d.tabu_inc && d.tabu_dec && d.ctl && vl_d && vpos_d && d.block_best && tc_d && th_d && hc_d &&
               d.hbins && d.hacc && h->t_rec && h->t_obj && h->t_xhat && h->t_s && h->t_dc && h->t_w && h->t_r && h->t_tabu &&
               (!lazy || (d.lz_s && d.lz_dc && d.lz_mark && d.lz_list)) && lc_d && tlg_d && tls_d &&
@@ -731,6 +742,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     d.ci_eq = ci_eq_d; d.cf_eq = cf_eq_d;
     d.row_ptr = row_ptr_d; d.col_idx = col_idx_d; d.row_val = row_val_d;
     d.rhs = rhs_d; d.eps = eps_d; d.row_int = rint_d; d.nrow_base = nrb_d;
+    d.res_rows = resr_d; d.n_res_int = n_res_int; d.m_norm = mn;
     d.vtype = vt_d; d.lb = lb_d; d.ub = ub_d; d.obj = obj_d;
     d.var_list = vl_d;
     d.vpos = vpos_d;
@@ -744,7 +756,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     UP(cf_ptr_d, cf_ptr.data(), n + 1); UP(cf_row_d, cf_row.data(), cf_row.size()); UP(cf_val_d, cf_val.data(), cf_val.size());
     UP(ci_eq_d, ci_eq.data(), n); UP(cf_eq_d, cf_eq.data(), n);
     UP(row_ptr_d, rp.data(), m + 1); UP(col_idx_d, p->col_idx, p->nnz); UP(row_val_d, row_val.data(), p->nnz);
-    UP(rhs_d, rhs.data(), m); UP(eps_d, eps.data(), m); UP(rint_d, rint.data(), m); UP(nrb_d, h->nrow_base.data(), m);
+    UP(rhs_d, rhs.data(), m); UP(eps_d, eps.data(), m); UP(rint_d, rint.data(), m); UP(nrb_d, h->nrow_base.data(), m); UP(resr_d, res_rows.data(), m);
     UP(vt_d, p->vtype, n); UP(lb_d, p->lb, n); UP(ub_d, p->ub, n); UP(obj_d, h->obj.data(), n);
     UP(vl_d, var_list.data(), var_list.size()); UP(vpos_d, vpos.data(), n);
     UP(tc_d, tiles_cta.data(), tiles_cta.size());
@@ -883,22 +895,20 @@ chap_status chap_bs_set_state(chap_bs *h, const double *x, const int32_t *w, int
 {
     if (!h) return CHAP_E_INVALID;
     if (mem != CHAP_MEM_HOST && mem != CHAP_MEM_DEVICE) return fail(h, CHAP_E_INVALID, "bad mem kind");
-    std::vector<double> xh;
+    if (mem == CHAP_MEM_HOST && x) return load_state(h, x, w, nullptr, nullptr, 0, 0, 0);
+    // device arrays are checked on the host, so they are read back first
+    std::vector<double> xh(h->n);
     std::vector<int> wh;
-    if (x) {
-        xh.resize(h->n);
-        if (mem == CHAP_MEM_HOST) std::copy(x, x + h->n, xh.begin());
-        else CK(h, cudaMemcpy(xh.data(), x, sizeof(double) * h->n, cudaMemcpyDeviceToHost), "read x");
-    } else {
-        xh.resize(h->n);
+    if (x) CK(h, cudaMemcpy(xh.data(), x, sizeof(double) * h->n, cudaMemcpyDeviceToHost), "read x");
+    else
         for (int j = 0; j < h->n; ++j) xh[j] = std::min(std::max(0.0, h->lb[j]), h->ub[j]);
-    }
-    if (w) {
+    const int *wp = w;
+    if (w && mem == CHAP_MEM_DEVICE) {
         wh.resize(h->m_norm);
-        if (mem == CHAP_MEM_HOST) std::copy(w, w + h->m_norm, wh.begin());
-        else CK(h, cudaMemcpy(wh.data(), w, sizeof(int) * h->m_norm, cudaMemcpyDeviceToHost), "read w");
+        CK(h, cudaMemcpy(wh.data(), w, sizeof(int) * h->m_norm, cudaMemcpyDeviceToHost), "read w");
+        wp = wh.data();
     }
-    return load_state(h, xh.data(), w ? wh.data() : nullptr, nullptr, nullptr, 0, 0, 0);
+    return load_state(h, xh.data(), wp, nullptr, nullptr, 0, 0, 0);
 }
 
 chap_status chap_bs_set_checkpoint(chap_bs *h, const double *x, const int32_t *w, const int64_t *tabu_inc,

@@ -215,7 +215,7 @@ struct RowBin {
 struct Dev {
     int n, m;
     int tenure;
-    int pad0;
+    int m_norm;              // normalised rows ("=" rows count twice)
     // CSC split, columns in var_list order (pointers indexed by position)
     const int *ci_ptr, *ci_row, *ci_val;
     const int *cf_ptr, *cf_row;
@@ -264,7 +264,10 @@ struct Dev {
     LCand *lcand;            // per tile: best candidate
     const LongCol *lcols;
     int n_long;
-    int pad2;
+    // rows of the residual computation (set-state only): the integral rows,
+    // then the others by decreasing length
+    int n_res_int;
+    const int *res_rows;
 };
 
 
@@ -325,7 +328,7 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
 cudaError_t launch_select_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
 cudaError_t launch_apply_gated(const Dev &d, const LaunchPlan &p, int gate, cudaStream_t st);
 cudaError_t launch_set_move(const Dev &d, int var, double new_value, cudaStream_t st);
-cudaError_t launch_residuals(const Dev &d, cudaStream_t st);
+cudaError_t launch_residuals(const Dev &d, const int *w, cudaStream_t st);
 cudaError_t launch_finish_set_state(const Dev &d, long long iter, long long best_nviol, int use_best, cudaStream_t st);
 cudaError_t launch_begin_run(const Dev &d, long long max_iters, int stop_at_feasible, cudaStream_t st);
 cudaError_t launch_set_cutoff(const Dev &d, int on, int row, int integral, double delta, double tol, cudaStream_t st);

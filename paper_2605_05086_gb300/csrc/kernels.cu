@@ -2541,51 +2541,146 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bump(Dev d, int gate)
 
 // --------------------------------------------------------- state handling
 
-// r = (sum of a x in CSR order) - b per physical row, one warp per row:
-// products are formed in parallel; integral rows sum them in int64 (exact, any
-// order), the others add them in CSR order so the residual is the same double
-// as a sequential evaluation.  Also sets the margins eps -+ r and counts the
-// violated normalised rows.
-__global__ void k_residuals(Dev d)
+// x_j + 0: a -0 from the caller is stored as +0, like every value the search
+// writes itself.
+__global__ void k_canon_x(Dev d)
 {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x)
+        d.x[j] = __dadd_rn(d.x[j], 0.0);
+}
+
+constexpr int kResProd = 15;                      // producer warps of a residual CTA
+constexpr int kResThreads = 32 * (kResProd + 1);  // plus the warp that adds
+constexpr int kResChunk = 128;                    // entries of each of 32 rows staged per phase
+constexpr int kResItems = (kResChunk + kResProd - 1) / kResProd;  // 32-entry pieces per producer lane
+constexpr int kResSmem = 2 * kResChunk * 33 * (int)sizeof(double);
+
+// Writes the whole state of physical row i from its sum y (double bits for a
+// non-integral row) and returns how many of its normalised halves are
+// violated.  Weights: w[k], w[k + 1] of the normalised rows (device), or 1.
+__device__ __forceinline__ int put_row_state(const Dev &d, const int *w, int i, long long ybits, bool integral)
+{
+    const int k = d.nrow_base[i];
+    const int kn = i + 1 < d.m ? d.nrow_base[i + 1] : d.m_norm;
+    RowState s;
+    s.w1 = w ? w[k] : 1;
+    s.w2 = kn - k == 2 ? (w ? w[k + 1] : 1) : -1;
+    int v;
+    if (integral) {
+        s.r = ybits - (long long)d.rhs[i];
+        s.m1 = 0.0;
+        s.m2 = 0.0;
+        v = (s.r > 0) + (s.w2 >= 0 && -s.r > 0);
+    } else {
+        const double r = __dsub_rn(__longlong_as_double(ybits), d.rhs[i]);
+        const double eps = d.eps[i];
+        s.r = __double_as_longlong(r);
+        s.m1 = __dsub_rn(eps, r);
+        s.m2 = __dadd_rn(eps, r);
+        v = dneg(s.m1) + (s.w2 >= 0 && dneg(s.m2));
+    }
+    d.rs[i] = s;
+    return v;
+}
+
+// Residuals at x (Sec. 3.1): r = (sum of a x in CSR order) - b per physical
+// row, the margins eps -+ r, the weights, and the count of violated
+// normalised rows (set-state only).
+//  - The first fp_ctas CTAs take the rows with floating-point data, 32 rows
+//    per CTA in decreasing length (res_rows).  Each lane of warp 0 owns one
+//    row and adds its products in CSR order, so the residual is the same
+//    double as a sequential evaluation, and no lane repeats another lane's
+//    adds.  The other kResProd warps form the products of the next phase
+//    (kResChunk entries of each row, 32 consecutive entries of one row per
+//    warp load, every load of a lane issued before its first gather) into
+//    the other half of a shared-memory double buffer.  The add chains of the
+//    longest rows set the kernel's duration: a phase is as long as the
+//    slower of its kResChunk dependent adds and one round of gathers.
+//  - The other CTAs take the integral rows, one warp per row, summing in
+//    int64 (exact in any order).
+__global__ void __launch_bounds__(kResThreads) k_residuals(Dev d, const int *w, int fp_ctas)
+{
+    extern __shared__ double res_stage[];  // [2][kResChunk][33]
+    __shared__ long long s_p0[32];
+    __shared__ int s_len[32];
+    __shared__ int s_lmax;
     const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int wib = threadIdx.x >> 5;
     long long local = 0;
-    for (int i = wid; i < d.m; i += nw) {
-        const long long p0 = d.row_ptr[i], p1 = d.row_ptr[i + 1];
-        RowState *p = d.rs + i;
-        if (d.row_int[i]) {
+    if ((int)blockIdx.x < fp_ctas) {
+        const int n_fp = d.m - d.n_res_int;
+        int i = -1;
+        if (wib == 0) {
+            const int q = blockIdx.x * 32 + lane;
+            long long p0 = 0;
+            int len = 0;
+            if (q < n_fp) {
+                i = d.res_rows[d.n_res_int + q];
+                p0 = d.row_ptr[i];
+                len = (int)(d.row_ptr[i + 1] - p0);
+            }
+            s_p0[lane] = p0;
+            s_len[lane] = len;
+            int lmax = len;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) lmax = max(lmax, __shfl_xor_sync(FULLMASK, lmax, off));
+            if (lane == 0) s_lmax = lmax;
+        }
+        __syncthreads();
+        const int nch = (s_lmax + kResChunk - 1) / kResChunk;
+        const int len = s_len[lane];
+        double y = 0.0;
+        for (int ph = 0; ph <= nch; ++ph) {
+            if (wib > 0 && ph < nch) {
+                // pieces it = wib - 1 + kResProd * u of this phase: row it / (kResChunk / 32),
+                // entries c0 + 32 (it % (kResChunk / 32)) + lane
+                double *t = res_stage + (ph & 1) * (kResChunk * 33);
+                const int c0 = ph * kResChunk;
+                int col[kResItems];
+                double a[kResItems], xv[kResItems];
+#pragma unroll
+                for (int u = 0; u < kResItems; ++u) {
+                    const int it = wib - 1 + kResProd * u;
+                    const int rr = it / (kResChunk / 32);
+                    const int k = c0 + 32 * (it % (kResChunk / 32)) + lane;
+                    col[u] = -1;
+                    a[u] = 0.0;
+                    if (it < kResChunk && k < s_len[rr]) {
+                        const long long e = s_p0[rr] + k;
+                        col[u] = __ldg(d.col_idx + e);
+                        a[u] = __ldg(d.row_val + e);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kResItems; ++u) xv[u] = col[u] >= 0 ? __ldg(d.x + col[u]) : 0.0;
+#pragma unroll
+                for (int u = 0; u < kResItems; ++u) {
+                    const int it = wib - 1 + kResProd * u;
+                    if (it < kResChunk) {
+                        const int rr = it / (kResChunk / 32);
+                        const int kk = 32 * (it % (kResChunk / 32)) + lane;
+                        t[kk * 33 + rr] = col[u] >= 0 ? __dmul_rn(a[u], xv[u]) : 0.0;
+                    }
+                }
+            }
+            if (wib == 0 && ph > 0) {
+                const double *t = res_stage + ((ph - 1) & 1) * (kResChunk * 33);
+                const int cnt = min(kResChunk, len - (ph - 1) * kResChunk);
+                for (int k = 0; k < cnt; ++k) y = __dadd_rn(y, t[k * 33 + lane]);
+            }
+            __syncthreads();
+        }
+        if (wib == 0 && i >= 0) local = put_row_state(d, w, i, __double_as_longlong(y), false);
+    } else {
+        const int nw = (gridDim.x - fp_ctas) * (kResThreads / 32);
+        for (int g = (blockIdx.x - fp_ctas) * (kResThreads / 32) + wib; g < d.n_res_int; g += nw) {
+            const int i = d.res_rows[g];
+            const long long p0 = d.row_ptr[i], p1 = d.row_ptr[i + 1];
             long long y = 0;
             for (long long e = p0 + lane; e < p1; e += 32) y += (long long)d.row_val[e] * (long long)d.x[d.col_idx[e]];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(FULLMASK, y, off);
-            if (lane == 0) {
-                const long long r = y - (long long)d.rhs[i];
-                p->r = r;
-                p->m1 = 0.0;
-                p->m2 = 0.0;
-                local += (r > 0) + (p->w2 >= 0 && -r > 0);
-            }
-        } else {
-            double y = 0.0;
-            for (long long e0 = p0; e0 < p1; e0 += 32) {
-                const long long e = e0 + lane;
-                const double t = e < p1 ? __dmul_rn(d.row_val[e], d.x[d.col_idx[e]]) : 0.0;
-                const int cnt = (int)min(32LL, p1 - e0);
-                for (int k = 0; k < cnt; ++k) {
-                    const double tk = __shfl_sync(FULLMASK, t, k);
-                    y = __dadd_rn(y, tk);
-                }
-            }
-            if (lane == 0) {
-                const double r = __dsub_rn(y, d.rhs[i]);
-                const double eps = d.eps[i];
-                p->r = __double_as_longlong(r);
-                p->m1 = __dsub_rn(eps, r);
-                p->m2 = __dadd_rn(eps, r);
-                local += dneg(p->m1) + (p->w2 >= 0 && dneg(p->m2));
-            }
+            if (lane == 0) local += put_row_state(d, w, i, y, true);
         }
     }
 #pragma unroll
@@ -2983,9 +3078,16 @@ cudaError_t launch_set_move(const Dev &d, int var, double nv, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_residuals(const Dev &d, cudaStream_t st)
+cudaError_t launch_residuals(const Dev &d, const int *w, cudaStream_t st)
 {
-    k_residuals<<<grid_for((long long)d.m * 32, 256, 152 * 8), 256, 0, st>>>(d);
+    k_canon_x<<<grid_for(d.n, 256), 256, 0, st>>>(d);
+    const int n_fp = d.m - d.n_res_int;
+    const int fp_ctas = (n_fp + 31) / 32;
+    const int int_ctas = d.n_res_int > 0 ? std::min((d.n_res_int + kResThreads / 32 - 1) / (kResThreads / 32), 152 * 3) : 0;
+    if (fp_ctas + int_ctas == 0) return cudaGetLastError();
+    cudaError_t e = raise_smem_limit((const void *)k_residuals, 6, kResSmem);
+    if (e != cudaSuccess) return e;
+    k_residuals<<<fp_ctas + int_ctas, kResThreads, kResSmem, st>>>(d, w, fp_ctas);
     return cudaGetLastError();
 }
 
