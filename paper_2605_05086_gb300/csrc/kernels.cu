@@ -155,6 +155,18 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 __device__ __forceinline__ int4 ld_row16(const RowState *p) { return __ldg(reinterpret_cast<const int4 *>(p)); }
 
+// The whole 32-byte row state in one 256-bit load: one L1 wavefront per lane
+// instead of one for each 16-byte half (the per-nonzero gathers of the
+// evaluation kernels are bound by these wavefronts).  Row states are 32-byte
+// aligned and not written while an evaluation kernel runs.
+__device__ __forceinline__ void ld_row32(const RowState *p, int4 &s0, int4 &s1)
+{
+    unsigned long long a, b, c, e;
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(e) : "l"(p));
+    s0 = make_int4((int)(unsigned)a, (int)(unsigned)(a >> 32), (int)(unsigned)b, (int)(unsigned)(b >> 32));
+    s1 = make_int4((int)(unsigned)c, (int)(unsigned)(c >> 32), (int)(unsigned)e, (int)(unsigned)(e >> 32));
+}
+
 __device__ __forceinline__ long long row_r(const int4 &v)
 {
     return (long long)(((unsigned long long)(unsigned)v.y << 32) | (unsigned)v.x);
@@ -493,9 +505,8 @@ __device__ __forceinline__ void bin_part(const Dev &d, int e0, int n, int nmax, 
         if (!FP) {
             s0 = ok ? ld_row16(d.rs + row) : z4;
         } else {
-            const int4 *p = reinterpret_cast<const int4 *>(d.rs + row);
-            s0 = ok ? __ldg(p) : z4;
-            s1 = ok ? __ldg(p + 1) : z4;
+            s0 = z4;
+            if (ok) ld_row32(d.rs + row, s0, s1);
         }
         const int vn = base + G + sub;
         const bool okn = vn < n;

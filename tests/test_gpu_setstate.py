@@ -1,7 +1,7 @@
 """Loading a state (chap_bs_set_state, chap_bs_set_checkpoint) recomputes every
 row's residual on the device: integral rows in int64, the others as the double
 sum of their products in CSR order, one lane per row with the products staged
-64 entries at a time.  The residuals, margins and violation count must equal
+128 entries at a time.  The residuals, margins and violation count must equal
 the oracle's bit for bit, on rows shorter and longer than one staging phase,
 with given weights, and with -0 in x (stored as +0)."""
 import numpy as np
@@ -66,7 +66,7 @@ def check(bs, orc, x):
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_residuals_across_phase_boundaries(chap, seed):
-    lengths = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 640, 1000, 2500] * 3
+    lengths = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 255, 256, 257, 640, 1000, 2500] * 3
     prob = rows_of_lengths(seed, lengths)
     orc = Oracle(prob)
     bs = chap.BestShift(prob, tenure=5)
