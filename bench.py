@@ -417,7 +417,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="general_200k",
                     choices=sorted(inst.WORKLOADS) + ["batch_64x4", "learned_200k", "learned_general", "multiclimb_200k"])
-    ap.add_argument("--batch-cap", type=int, default=20000, help="iteration cap per chain (batch_64x4)")
+    ap.add_argument("--batch-cap", type=int, default=100000, help="iteration cap per chain (batch_64x4)")
     ap.add_argument("--learned-cap", type=int, default=300000, help="iteration cap (learned_200k)")
     ap.add_argument("--propose-every", type=int, default=50, help="iterations between proposals (learned_200k)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
