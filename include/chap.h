@@ -121,8 +121,9 @@ typedef struct chap_options {
     int32_t static_scratch_only; /* create time, default 0: see chap_bs_best_shift_static_scratch */
     int32_t shard_rank;          /* create time: column shard of this handle (see chap_bs_move_record) */
     int32_t shard_count;         /* create time, default 0 or 1: the handle evaluates every column */
-    int32_t bin_kernel;          /* create time: binary flips 0 automatic, 1 column-wise, 2 row-wise */
-    int32_t reserved[2];
+    int32_t bin_kernel;          /* create time: binary flips 0 automatic, 1 column-wise, 2 row-wise, 3 row-blocked */
+    int32_t bin_block_rows;      /* create time: rows of one row block of bin_kernel 3 (0: 8192; 1..8192) */
+    int32_t reserved;
 } chap_options;
 
 /* One move.  var = -1 means "no admissible variable has a positive score": the
@@ -166,7 +167,7 @@ typedef struct chap_info {
     int32_t n_long_cols;      /* columns on the multi-CTA merge-sort path (lists over 8192 entries) */
     int32_t n_cta_cols;       /* columns on the one-CTA shared-memory sort path (129..8192 entries) */
     int32_t bin_rows;         /* 1: binary flips scored row-wise (clusters over column blocks) */
-    int32_t reserved;
+    int32_t bin_row_blocks;   /* > 0: binary flips row-blocked over this many row blocks (bin_kernel 3) */
 } chap_info;
 
 CHAP_API void chap_options_default(chap_options *opts);

@@ -51,7 +51,7 @@ class chap_options(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("tenure", C.c_int32), ("graph_iters", C.c_int32),
                 ("max_iters", C.c_int64), ("stop_at_feasible", C.c_int32), ("lazy_binary", C.c_int32),
                 ("static_scratch_only", C.c_int32), ("shard_rank", C.c_int32), ("shard_count", C.c_int32),
-                ("bin_kernel", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("bin_kernel", C.c_int32), ("bin_block_rows", C.c_int32), ("reserved", C.c_int32)]
 
 
 class chap_move(C.Structure):
@@ -87,7 +87,7 @@ class chap_info(C.Structure):
                 ("bytes_bin", C.c_int64), ("bytes_nb", C.c_int64), ("bytes_cta", C.c_int64),
                 ("bytes_hist", C.c_int64), ("bin_lanes", C.c_int32), ("nb_lanes", C.c_int32),
                 ("n_long_cols", C.c_int32), ("n_cta_cols", C.c_int32), ("bin_rows", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("bin_row_blocks", C.c_int32)]
 
 
 _lib = None

@@ -288,7 +288,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     if (!(h->opt.feas_tol >= 0.0) || h->opt.tenure < 0 || h->opt.graph_iters < 1 ||
         (h->opt.lazy_binary != 0 && h->opt.lazy_binary != 1) ||
         (h->opt.static_scratch_only != 0 && h->opt.static_scratch_only != 1) ||
-        h->opt.bin_kernel < 0 || h->opt.bin_kernel > 2 ||
+        h->opt.bin_kernel < 0 || h->opt.bin_kernel > 3 ||
+        h->opt.bin_block_rows < 0 || h->opt.bin_block_rows > kBlkRows ||
         h->opt.shard_count < 0 || (h->opt.shard_count > 1 && (h->opt.shard_rank < 0 ||
                                                               h->opt.shard_rank >= h->opt.shard_count))) {
         delete h;
@@ -626,7 +627,135 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         }
         rb_bytes += (int64_t)bin_cols * (4 + 8 + 8);
     }
-    const int n_tb = bin_rows ? rb_blocks * kRbCluster : (bin_cols > 0 ? bin_grid_size(bin_cols, bin_G) : 0);
+    // row-blocked binary flips (k_eval_bin_blk): option bin_kernel 3, or the
+    // library's choice (0) when the rows form few blocks, there are many binary
+    // columns and a column meets a block in enough entries on average (kept
+    // scores and the row-wise option keep their kernels)
+    const int blk_rows = h->opt.bin_block_rows > 0 ? (int)h->opt.bin_block_rows : kBlkRows;
+    const int nblk = m > 0 ? (m + blk_rows - 1) / blk_rows : 0;
+    const int64_t nnz_bin = (int64_t)(ci_ptr[bin_cols] - ci_ptr[0]) + (cf_ptr[bin_cols] - cf_ptr[0]);
+    bool bin_blk = false;
+    if (bin_cols > 0 && !lazy_bin && !bin_rows && nblk > 0) {
+        if (h->opt.bin_kernel == 3) {
+            if (bin_cols >= kBlkMaxPos) {
+                delete h;
+                std::fprintf(stderr, "chap_bs_create: row-blocked binary flips name at most %d binary positions\n",
+                             kBlkMaxPos - 1);
+                return CHAP_E_UNSUPPORTED;
+            }
+            bin_blk = true;
+        } else if (h->opt.bin_kernel == 0) {
+            bin_blk = nblk <= kBlkMaxBlocks && bin_cols >= kBlkMinCols && bin_cols < kBlkMaxPos &&
+                      (double)nnz_bin / ((double)nblk * bin_cols) >= kBlkMinSeg;
+        }
+    }
+    const int blk_nfin = bin_blk ? (bin_cols + kBlkFin - 1) / kBlkFin : 0;
+    std::vector<unsigned> blk_metaI, blk_metaF;
+    std::vector<int> blk_valI;
+    std::vector<double> blk_valF;
+    std::vector<BlkItem> blk_items;
+    int64_t blk_bytes = 0;
+    if (bin_blk) {
+        // per block the entries of each stream ordered by position, then row:
+        // count, offsets (cI / cF: first entry of position q in block b), fill
+        std::vector<int> cI((size_t)nblk * (bin_cols + 1), 0), cF((size_t)nblk * (bin_cols + 1), 0);
+        for (int q = 0; q < bin_cols; ++q) {
+            for (int e = ci_ptr[q]; e < ci_ptr[q + 1]; ++e) ++cI[(size_t)(ci_row[e] / blk_rows) * (bin_cols + 1) + q];
+            for (int e = cf_ptr[q]; e < cf_ptr[q + 1]; ++e) ++cF[(size_t)(cf_row[e] / blk_rows) * (bin_cols + 1) + q];
+        }
+        int tI = 0, tF = 0;
+        for (int b = 0; b < nblk; ++b)
+            for (int q = 0; q <= bin_cols; ++q) {
+                const size_t k = (size_t)b * (bin_cols + 1) + q;
+                const int a = cI[k], c = cF[k];
+                cI[k] = tI;
+                cF[k] = tF;
+                tI += a;
+                tF += c;
+            }
+        blk_metaI.resize(tI);
+        blk_valI.resize(tI);
+        blk_metaF.resize(tF);
+        blk_valF.resize(tF);
+        {
+            std::vector<int> fI(cI), fF(cF);
+            for (int q = 0; q < bin_cols; ++q) {
+                for (int e = ci_ptr[q]; e < ci_ptr[q + 1]; ++e) {
+                    const int b = ci_row[e] / blk_rows;
+                    const int k = fI[(size_t)b * (bin_cols + 1) + q]++;
+                    blk_metaI[k] = ((unsigned)q << kBlkRowBits) | (unsigned)(ci_row[e] - b * blk_rows);
+                    blk_valI[k] = ci_val[e];
+                }
+                for (int e = cf_ptr[q]; e < cf_ptr[q + 1]; ++e) {
+                    const int b = cf_row[e] / blk_rows;
+                    const int k = fF[(size_t)b * (bin_cols + 1) + q]++;
+                    blk_metaF[k] = ((unsigned)q << kBlkRowBits) | (unsigned)(cf_row[e] - b * blk_rows);
+                    blk_valF[k] = cf_val[e];
+                }
+            }
+        }
+        // padding: the kernel reads four entries at a time, past a stream's end
+        blk_metaI.resize(blk_metaI.size() + 8, 0u);
+        blk_valI.resize(blk_valI.size() + 8, 0);
+        blk_metaF.resize(blk_metaF.size() + 8, 0u);
+        blk_valF.resize(blk_valF.size() + 8, 0.0);
+        // work items: every block gets CTAs in proportion to its work (an
+        // integral entry 2, another 3, a position 1), at least one, one wave on
+        // the device; each block's positions are cut into spans of like work
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        auto work = [&](int b, int q) {   // work of block b's positions [0, q)
+            const size_t k = (size_t)b * (bin_cols + 1);
+            return 2LL * (cI[k + q] - cI[k]) + 3LL * (cF[k + q] - cF[k]) + q;
+        };
+        std::vector<int64_t> bw(nblk);
+        int64_t tot = 0;
+        for (int b = 0; b < nblk; ++b) { bw[b] = work(b, bin_cols); tot += bw[b]; }
+        std::vector<int> ncta(nblk);
+        int sum = 0;
+        for (int b = 0; b < nblk; ++b) {
+            ncta[b] = std::max<int>(1, (int)std::llround((double)sms * (double)bw[b] / (double)tot));
+            ncta[b] = std::min(ncta[b], bin_cols);
+            sum += ncta[b];
+        }
+        while (sum > std::max(sms, nblk)) {
+            int bmax = 0;
+            for (int b = 1; b < nblk; ++b)
+                if (ncta[b] > ncta[bmax]) bmax = b;
+            if (ncta[bmax] <= 1) break;
+            --ncta[bmax];
+            --sum;
+        }
+        for (int b = 0; b < nblk; ++b) {
+            const size_t k = (size_t)b * (bin_cols + 1);
+            int qa = 0;
+            for (int part = 1; part <= ncta[b]; ++part) {
+                int qb = bin_cols;
+                if (part < ncta[b]) {
+                    // first position at which the work reaches part / ncta of the block's
+                    const int64_t want = bw[b] * part / ncta[b];
+                    int lo = qa, hi = bin_cols;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) / 2;
+                        if (work(b, mid) >= want) hi = mid; else lo = mid + 1;
+                    }
+                    qb = lo;
+                }
+                if (qb > qa) blk_items.push_back(BlkItem{b, qa, qb, cI[k + qa], cI[k + qb], cF[k + qa], cF[k + qb], 0});
+                qa = std::max(qa, qb);
+            }
+        }
+        // algorithmic bytes of one launch: every entry once (word +
+        // coefficient), every row state and its integrality flag once, per
+        // position its variable, direction, tabu stamps and the accumulators
+        // read and cleared
+        blk_bytes = 8LL * tI + 12LL * tF + 33LL * m + (int64_t)bin_cols * (4 + 1 + 8 + 24);
+    }
+    const int n_tb = bin_blk ? blk_nfin
+                   : bin_rows ? rb_blocks * kRbCluster : (bin_cols > 0 ? bin_grid_size(bin_cols, bin_G) : 0);
     const int n_tc = (int)tiles_cta.size();
     const int slot_hist = n_tb + n_tn + n_tc;
     for (size_t q = 0; q < hcols.size(); ++q) hcols[q].slot = slot_hist + (int)q;
@@ -705,6 +834,24 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
         rbvi_d = dalloc<int>(h, rb_vi.size());
         rbvf_d = dalloc<double>(h, rb_vf.size());
     }
+    BinBlk bbd{};
+    if (bin_blk) {
+        d.bup = dalloc<unsigned char>(h, bin_cols);
+        d.n_bup = bin_cols;
+        bbd.nblk = nblk;
+        bbd.rows = blk_rows;
+        bbd.n_items = (int)blk_items.size();
+        bbd.n_fin = blk_nfin;
+        bbd.items = dalloc<BlkItem>(h, blk_items.size());
+        bbd.metaI = dalloc<unsigned>(h, blk_metaI.size());
+        bbd.metaF = dalloc<unsigned>(h, blk_metaF.size());
+        bbd.valI = dalloc<int>(h, blk_valI.size());
+        bbd.valF = dalloc<double>(h, blk_valF.size());
+        bbd.acc_s = dalloc<long long>(h, bin_cols);
+        bbd.acc_dc = dalloc<int>(h, bin_cols);
+    }
+    const bool blk_ok = !bin_blk || (d.bup && bbd.items && bbd.metaI && bbd.metaF && bbd.valI && bbd.valF &&
+                                     bbd.acc_s && bbd.acc_dc);
     LongCol *lc_d = dalloc<LongCol>(h, lcols.size());
     Tile *tlg_d = dalloc<Tile>(h, tiles_lgen.size()), *tls_d = dalloc<Tile>(h, tiles_lscan.size());
     d.n_long = (int)lcols.size();
@@ -724,6 +871,7 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
               (!has_long || (d.lbuf0 && d.lbuf1 && d.lacc && d.ltsum && d.ltsumc && d.lcand)) &&
               (!bin_rows || (rbr_d[0] && rbr_d[1] && rbe_d[0] && rbe_d[1] && rbs_d[0] && rbs_d[1] && rbc_d[0] &&
                              rbc_d[1] && rbo_d[0] && rbo_d[1] && rbvi_d && rbvf_d));
+    ok = ok && blk_ok;
     if (ok && cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { cudaGetLastError(); h->h_ctl = nullptr; ok = false; }
     if (ok && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ok = false; }
     for (int k = 0; k < 3 && ok; ++k)
@@ -769,6 +917,15 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     }
     if (bin_rows) { UP(rbvi_d, rb_vi.data(), rb_vi.size()); UP(rbvf_d, rb_vf.data(), rb_vf.size()); }
     UP(tlg_d, tiles_lgen.data(), tiles_lgen.size()); UP(tls_d, tiles_lscan.data(), tiles_lscan.size());
+    if (bin_blk) {
+        UP(const_cast<BlkItem *>(bbd.items), blk_items.data(), blk_items.size());
+        UP(const_cast<unsigned *>(bbd.metaI), blk_metaI.data(), blk_metaI.size());
+        UP(const_cast<unsigned *>(bbd.metaF), blk_metaF.data(), blk_metaF.size());
+        UP(const_cast<int *>(bbd.valI), blk_valI.data(), blk_valI.size());
+        UP(const_cast<double *>(bbd.valF), blk_valF.data(), blk_valF.size());
+        if (e == cudaSuccess) e = cudaMemsetAsync(bbd.acc_s, 0, sizeof(long long) * (size_t)bin_cols, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bbd.acc_dc, 0, sizeof(int) * (size_t)bin_cols, st);
+    }
 #undef UP
     if (e == cudaSuccess && has_long) e = cudaMemsetAsync(d.lacc, 0, sizeof(HistAcc) * lcols.size(), st);
     if (e == cudaSuccess && hist_bins > 0 && !h->no_hist_scratch)
@@ -783,6 +940,8 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     pl.lazy_mark_blocks = 64;
     pl.bin_cols = bin_cols; pl.n_bin = n_tb; pl.bin_G = bin_G;
     pl.bin_rows = bin_rows ? 1 : 0;
+    pl.bin_blk = bin_blk ? 1 : 0;
+    pl.bb = bbd;
     pl.rb = RowBin{rb_blocks, 0, rbr_d[0], rbe_d[0], rbc_d[0], rbo_d[0], rbvi_d, rbr_d[1], rbe_d[1], rbc_d[1],
                    rbo_d[1], rbvf_d, rbs_d[0], rbs_d[1]};
     pl.nb_q0 = kind_base[T_NB]; pl.nb_cols = nb_cols; pl.nb_grid = n_tn; pl.nb_G = nb_G;
@@ -807,13 +966,13 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
     in.n = n; in.m = m; in.m_norm = mn;
     in.n_bin = n_bin; in.n_int = n_int; in.n_cont = n_cont; in.n_fixed = n_fixed;
     in.nnz = p->nnz; in.nnz_int_rows = nnz_int; in.nnz_fp_rows = p->nnz - nnz_int;
-    in.eval_blocks = n_tb + n_tn + n_tc + (int)tiles_hist.size() + (int)tiles_lscan.size();
+    in.eval_blocks = (bin_blk ? (int)blk_items.size() : n_tb) + n_tn + n_tc + (int)tiles_hist.size() + (int)tiles_lscan.size();
     in.n_hist_cols = (int)hcols.size();
     in.n_long_cols = (int)lcols.size();
     in.n_cta_cols = n_tc;
     // evaluation kernels (they also select the move), a selection kernel only
     // when none runs, the move apply and the weight bump
-    in.launches_per_step = (n_tb > 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + (n_bb == 0) + 2 +
+    in.launches_per_step = (n_tb > 0) + (bin_blk ? 1 : 0) + (n_tn > 0) + (n_tc > 0) + (!tiles_hist.empty()) + (n_bb == 0) + 2 +
                            (lazy ? 2 : 0) +   // kept binary scores: the scan and the marking kernel
                            (has_long ? 3 + long_rounds : 0);   // long lists: generation, merges, tile sums, scan
     // algorithmic bytes of one pass: every nonzero once (row + coefficient),
@@ -835,11 +994,13 @@ chap_status chap_bs_create(const chap_problem *p, const chap_options *opts, void
                 if (touched[i]) b += rint[i] ? 16 : 32;
             return b + per_col * (q1 - q0);
         };
-        in.grid_bin = n_tb;
+        in.grid_bin = bin_blk ? (int)blk_items.size() : n_tb;
+        in.bin_row_blocks = bin_blk ? nblk : 0;
         in.bin_lanes = bin_G;
         in.grid_nb = n_tn;
         in.nb_lanes = nb_G;
-        in.bytes_bin = !bin_cols ? 0 : bin_rows ? rb_bytes : kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16);
+        in.bytes_bin = !bin_cols ? 0 : bin_blk ? blk_bytes : bin_rows ? rb_bytes
+                                                        : kernel_bytes(kind_base[T_BIN], kind_base[T_BIN + 1], 4 + 8 + 16);
         in.bin_rows = bin_rows ? 1 : 0;
         in.bytes_nb = nb_cols ? kernel_bytes(kind_base[T_NB], kind_base[T_NB + 1], 4 + 8 + 16 + 1 + 8 + 16) : 0;
         const int ncta = kind_base[T_NB_CTA + 1] - kind_base[T_NB_CTA];

@@ -212,6 +212,42 @@ struct RowBin {
     const int *split_i, *split_f;     // per block: kRbCluster + 1 row-list boundaries of the CTAs
 };
 
+// Row-blocked binary flips (k_eval_bin_blk).  The physical rows are cut into
+// blocks of at most 8192 consecutive rows; one CTA copies a block's row states
+// into shared memory (24 B a row: r or eps - r, eps + r, both weights) and
+// scores the binary entries whose rows lie in that block, for a span of
+// binary positions: the row-state lookups become shared-memory loads instead
+// of one L2 gather per nonzero.  Per block, the entries on integral rows and
+// on the other rows form two streams ordered by position, then row; an entry
+// is a 32-bit word (position << 13 | row inside the block) and its int32 /
+// double coefficient.  Every work item (block, position span, the span's
+// entry ranges of both streams) is split evenly over the CTA's warps, which
+// stream their entries 32 at a time and sum each position's terms with a
+// segmented warp scan; the blocks' partial sums meet in acc_s / acc_dc
+// (device atomics, zero between passes).  A second kernel, one CTA per
+// finalize range of kBlkFin positions, applies tabu and aspiration to the
+// sums, writes the range's candidate slot and returns the accumulators to
+// zero.
+struct BlkItem {
+    int b;                         // row block
+    int q0, q1;                    // position span [q0, q1)
+    int eI0, eI1, eF0, eF1;        // its entries in the two streams
+    int pad;
+};
+
+struct BinBlk {
+    int nblk;                      // row blocks
+    int rows;                      // rows per block (kBlkRows unless set smaller at create)
+    int n_items;                   // work items = CTAs of one launch
+    int n_fin;                     // finalize ranges (= CTAs of the finalize kernel = candidate slots)
+    const BlkItem *items;
+    const unsigned *metaI, *metaF; // position << 13 | row inside the block
+    const int *valI;
+    const double *valF;
+    long long *acc_s;
+    int *acc_dc;
+};
+
 struct Dev {
     int n, m;
     int tenure;
@@ -268,6 +304,10 @@ struct Dev {
     // then the others by decreasing length
     int n_res_int;
     const int *res_rows;
+    // row-blocked binary flips only (else null / 0): per binary position 1 when
+    // x of its variable is 0 (the flip raises it), kept by every x update
+    unsigned char *bup;
+    int n_bup;
 };
 
 
@@ -302,6 +342,8 @@ struct LaunchPlan {
     int lazy;                  // binary flips through the kept scores (k_eval_bin_lazy, k_bin_scan)
     int bin_rows;              // binary flips row-wise (k_eval_bin_rows, n_bin = blocks * kRbCluster CTAs)
     RowBin rb;
+    int bin_blk;               // binary flips row-blocked (k_eval_bin_blk, bb.n_items CTAs; k_bin_blk_final, n_bin = bb.n_fin)
+    BinBlk bb;
     int lazy_mark_blocks;      // CTAs of the marking kernel
     int apply_blocks;          // CTAs of the weight bump
     int apply_move_blocks;     // CTAs of the move apply (longest column / kApplyMoveThreads)
@@ -361,6 +403,15 @@ constexpr int kLongThreads = 512;
 constexpr int kLongTile = 2048;        // entries per scan CTA (4 per thread)
 constexpr int kStaticHistBins = 1 << 16;  // fixed counting-sort scratch: bins (24 B each, 1.5 MiB)
 constexpr int kStaticHistCols = 256;      // and columns
+constexpr int kBlkRows = 8192;          // rows of one row block of the row-blocked binary flips (24 B each in shared memory)
+constexpr int kBlkRowBits = 13;        // bits of the row inside a block in an entry word (kBlkRows = 2^13)
+constexpr int kBlkMaxPos = 1 << (32 - kBlkRowBits);  // binary positions an entry word can name
+constexpr int kBlkThreads = 1024;
+constexpr int kBlkFin = 1024;           // binary positions of one finalize range (one CTA)
+constexpr int kBlkFinThreads = 256;
+constexpr int kBlkMaxBlocks = 32;       // the library picks the row-blocked flips up to this many row blocks,
+constexpr int kBlkMinCols = 16384;      // from this many binary columns,
+constexpr double kBlkMinSeg = 2.0;      // and from this many entries per (block, column) on average
 constexpr int kApplyThreads = 256;
 constexpr int kApplyMoveThreads = 1024;
 constexpr int kLazyMaxRows = 2048;      // longer moved columns re-evaluate every kept binary score

@@ -729,6 +729,245 @@ __global__ void __launch_bounds__(kRbThreads) k_eval_bin_rows(Dev d, RowBin rb, 
     finish_pass(d);
 }
 
+// ------------------------------------------------ row-blocked binary flips
+//
+// The layout is described with BinBlk (chap_internal.h).  k_eval_bin_blk: one
+// CTA per work item (row block, position span); the block's row states are
+// copied into shared memory once, then each warp streams its share of the
+// span's entries of both streams, four consecutive entries per lane (16-byte
+// loads of the entry words and coefficients; shared-memory row states; the
+// penalty changes of both halves, the second only on an "=" row, w2 >= 0).
+// A lane sums its entries by position; the runs that lie inside the lane are
+// added to their positions' accumulators at once, and one segmented warp scan
+// joins the runs that cross lanes.  k_bin_blk_final: one CTA per finalize
+// range applies tabu and aspiration to the positions' sums (as k_eval_bin
+// does), writes the range's candidate slot and returns the accumulators to
+// zero.
+
+constexpr int kBlkWarps = kBlkThreads / 32;
+static_assert(kBlkRows == 1 << kBlkRowBits, "an entry word holds the row inside a block");
+
+__host__ __device__ constexpr int blk_smem(int rows) { return rows * (2 * (int)sizeof(long long) + (int)sizeof(int2)); }
+
+// Flip terms of one entry of an integral row: residual r, weights w (w.y < 0
+// on a single row), change ad of the residual.
+__device__ __forceinline__ void blk_int(long long r, int2 w, int ad, long long &s, int &dc)
+{
+    const long long r1 = r + ad;
+    const bool v0 = r > 0, v1 = r1 > 0;
+    s += (long long)flip_f(v0, v1, ad < 0) * w.x;
+    dc += (int)v1 - (int)v0;
+    if (w.y >= 0) {
+        const bool u0 = r < 0, u1 = r1 < 0;
+        s += (long long)flip_f(u0, u1, ad > 0) * w.y;
+        dc += (int)u1 - (int)u0;
+    }
+}
+
+// Flip terms of one entry of a non-integral row: margins m1 = eps - r and
+// (read only on an "=" row) m2 = eps + r, change ad of the residual.
+__device__ __forceinline__ void blk_fp(double m1, const long long *m2p, int2 w, double ad, long long &s, int &dc)
+{
+    const bool neg = dneg(ad);
+    const bool v0 = dneg(m1), v1 = dgt(ad, m1);
+    s += (long long)flip_f(v0, v1, neg) * w.x;
+    dc += (int)v1 - (int)v0;
+    if (w.y >= 0) {
+        const double m2 = __longlong_as_double(*m2p);
+        const bool u0 = dneg(m2), u1 = dgt(dflip(ad), m2);
+        s += (long long)flip_f(u0, u1, !neg) * w.y;
+        dc += (int)u1 - (int)u0;
+    }
+}
+
+__device__ __forceinline__ void blk_add(const BinBlk &bb, int q, long long s, int dc)
+{
+    if (s) atomicAdd(reinterpret_cast<unsigned long long *>(bb.acc_s + q), (unsigned long long)s);
+    if (dc) atomicAdd(bb.acc_dc + q, dc);
+}
+
+// Terms of one entry: word mw, coefficient av (position q; no entry: q < 0).
+template <bool FP, typename Val>
+__device__ __forceinline__ void blk_entry(const Dev &d, const long long *sA, const long long *sB, const int2 *sW,
+                                          unsigned mw, Val av, int q, long long &s, int &dc)
+{
+    s = 0;
+    dc = 0;
+    if (q < 0) return;
+    const int l = (int)(mw & ((1u << kBlkRowBits) - 1u));
+    const bool up = __ldg(d.bup + q) != 0;
+    const int2 w = sW[l];
+    if (!FP) blk_int(sA[l], w, up ? (int)av : -(int)av, s, dc);
+    else blk_fp(__longlong_as_double(sA[l]), sB + l, w, up ? (double)av : dflip((double)av), s, dc);
+}
+
+// One warp's entries [a, b) of one stream (FP: the non-integral rows), in
+// rounds of 128: lane k holds entries base + 4k .. base + 4k + 3 (base a
+// multiple of 4; the arrays are padded past their end).  Positions ascend
+// along the entries; entries outside [a, b) take the key -1 before a and
+// INT_MAX after b and add nothing.
+template <bool FP>
+__device__ __forceinline__ void blk_stream(const Dev &d, const BinBlk &bb, const long long *sA, const long long *sB,
+                                           const int2 *sW, int a, int b, int lane)
+{
+    using Val = typename std::conditional<FP, double, int>::type;
+    const unsigned *metap = FP ? bb.metaF : bb.metaI;
+    const Val *valp = reinterpret_cast<const Val *>(FP ? (const void *)bb.valF : (const void *)bb.valI);
+    // the next round's words and coefficients are loaded before this round's
+    // terms are computed
+    unsigned nw[4];
+    Val nv[4];
+    auto load = [&](int e) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { nw[k] = 0u; nv[k] = Val(1); }
+        if (e + 3 >= a && e < b) {
+            const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(metap + e));
+            nw[0] = m4.x; nw[1] = m4.y; nw[2] = m4.z; nw[3] = m4.w;
+            if (FP) {
+                const double2 v0 = __ldg(reinterpret_cast<const double2 *>(valp + e));
+                const double2 v1 = __ldg(reinterpret_cast<const double2 *>(valp + e + 2));
+                nv[0] = (Val)v0.x; nv[1] = (Val)v0.y; nv[2] = (Val)v1.x; nv[3] = (Val)v1.y;
+            } else {
+                const int4 v = __ldg(reinterpret_cast<const int4 *>(valp + e));
+                nv[0] = (Val)v.x; nv[1] = (Val)v.y; nv[2] = (Val)v.z; nv[3] = (Val)v.w;
+            }
+        }
+    };
+    load((a & ~3) + 4 * lane);
+    for (int base = a & ~3; base < b; base += 128) {
+        const int e = base + 4 * lane;
+        unsigned mw[4];
+        Val av[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { mw[k] = nw[k]; av[k] = nv[k]; }
+        load(e + 128);
+        int key[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) key[k] = e + k < a ? -1 : (e + k >= b ? INT_MAX : (int)(mw[k] >> kBlkRowBits));
+        // the lane's runs: the first (key[0]) and the last (key[3]) may
+        // continue in the neighbouring lanes, the ones between are complete
+        long long sa = 0, sz = 0;
+        int da = 0, dz = 0;
+        int cur = key[0];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            long long s;
+            int dc;
+            blk_entry<FP>(d, sA, sB, sW, mw[k], av[k], (key[k] >= 0 && key[k] != INT_MAX) ? key[k] : -1, s, dc);
+            if (key[k] != cur) {
+                // the run of cur ends here: the first run is kept, a middle one is added
+                if (cur != key[0] && cur >= 0 && cur != INT_MAX) blk_add(bb, cur, sz, dz);
+                else if (cur == key[0]) { sa = sz; da = dz; }
+                sz = 0;
+                dz = 0;
+                cur = key[k];
+            }
+            sz += s;
+            dz += dc;
+        }
+        const bool uni = key[0] == key[3];
+        if (uni) { sa = 0; da = 0; }   // one run: all of it is in sz
+        // segmented scan of the last runs: a lane continues its left
+        // neighbour's last run when it is one run of the same key
+        const int prev3 = __shfl_up_sync(FULLMASK, key[3], 1), next0 = __shfl_down_sync(FULLMASK, key[0], 1);
+        long long v = sz;
+        int vd = dz;
+        int f = (lane == 0 || !uni || prev3 != key[0]) ? 1 : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long ts = __shfl_up_sync(FULLMASK, v, o);
+            const int td = __shfl_up_sync(FULLMASK, vd, o), tf = __shfl_up_sync(FULLMASK, f, o);
+            if (lane >= o) {
+                if (!f) { v += ts; vd += td; }
+                f |= tf;
+            }
+        }
+        // a lane of several runs closes its first run with the left
+        // neighbour's open sum (when that one continues into it)
+        const long long lv = __shfl_up_sync(FULLMASK, v, 1);
+        const int lvd = __shfl_up_sync(FULLMASK, vd, 1);
+        if (!uni && key[0] >= 0 && key[0] != INT_MAX) {
+            const bool join = lane > 0 && prev3 == key[0];
+            blk_add(bb, key[0], sa + (join ? lv : 0), da + (join ? lvd : 0));
+        }
+        // the last run is added by the lane where it ends
+        if ((lane == 31 || next0 != key[3]) && key[3] >= 0 && key[3] != INT_MAX) blk_add(bb, key[3], v, vd);
+    }
+}
+
+__global__ void __launch_bounds__(kBlkThreads, 1) k_eval_bin_blk(Dev d, BinBlk bb, int gate)
+{
+    if (gated_done(d, gate)) return;
+    extern __shared__ __align__(16) unsigned char blk_smem_raw[];
+    long long *sA = reinterpret_cast<long long *>(blk_smem_raw);   // r (integral row) or eps - r
+    long long *sB = sA + bb.rows;                                   // eps + r (other rows)
+    int2 *sW = reinterpret_cast<int2 *>(sB + bb.rows);              // w1, w2
+    const BlkItem it = bb.items[blockIdx.x];
+    const int r0 = it.b * bb.rows, nr = min(bb.rows, d.m - r0);
+    // kBlkRows / kBlkThreads rows per thread, their loads issued together
+#pragma unroll
+    for (int k = 0; k < kBlkRows / kBlkThreads; ++k) {
+        const int l = k * kBlkThreads + (int)threadIdx.x;
+        if (l < nr) {
+            int4 s0, s1;
+            ld_row32(d.rs + r0 + l, s0, s1);
+            const bool integ = __ldg(d.row_int + r0 + l) != 0;
+            sA[l] = integ ? row_r(s0) : row_r(s1);
+            sB[l] = (long long)(((unsigned long long)(unsigned)s1.w << 32) | (unsigned)s1.z);
+            sW[l] = make_int2(s0.z, s0.w);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the warps' shares of each stream, cut at multiples of 4 entries
+    auto cut = [&](int e0, int e1, int k) {
+        if (k <= 0) return e0;
+        if (k >= kBlkWarps) return e1;
+        const int c = (int)(e0 + (long long)(e1 - e0) * k / kBlkWarps) & ~3;
+        return max(e0, c);
+    };
+    blk_stream<false>(d, bb, sA, sB, sW, cut(it.eI0, it.eI1, warp), cut(it.eI0, it.eI1, warp + 1), lane);
+    blk_stream<true>(d, bb, sA, sB, sW, cut(it.eF0, it.eF1, warp), cut(it.eF0, it.eF1, warp + 1), lane);
+}
+
+__global__ void __launch_bounds__(kBlkFinThreads) k_bin_blk_final(Dev d, BinBlk bb, int ncols, VarOut o, int gate)
+{
+    if (gated_done(d, gate)) return;
+    const long long iter = d.ctl->iter, nviol = d.ctl->nviol, bestnv = d.ctl->best_nviol;
+    Cand best{0, kNoVar, 0, 0.0};
+    for (int q = blockIdx.x * kBlkFin + threadIdx.x; q < min(ncols, (blockIdx.x + 1) * kBlkFin); q += blockDim.x) {
+        const long long s = bb.acc_s[q];
+        const int dc = bb.acc_dc[q];
+        bb.acc_s[q] = 0;
+        bb.acc_dc[q] = 0;
+        const int j = __ldg(d.var_list + q);
+        const bool up = d.bup[q] != 0;
+        bool mv = s > 0;
+        if (mv) {
+            const int stamp = up ? d.tabu_inc[j] : d.tabu_dec[j];
+            mv = iter >= (long long)stamp || nviol + (long long)dc < bestnv;
+        }
+        const double xh = up ? 1.0 : 0.0;
+        if (o.xhat) o.xhat[j] = mv ? xh : d.x[j];
+        if (o.s) o.s[j] = mv ? s : 0;
+        if (o.dc) o.dc[j] = mv ? dc : 0;
+        if (mv && cand_better(s, j, best.s, best.var)) best = Cand{s, j, dc, xh};
+    }
+    const Cand cb = block_reduce_cand(best);
+    if (threadIdx.x == 0) {
+        d.block_best[blockIdx.x] = cb;
+        if (cb.s > 0) atomicMax(&d.ctl->pass_best, cb.s);
+    }
+    finish_pass(d);
+}
+
+// Flip direction of every binary position from x (after a new state).
+__global__ void k_bup_init(Dev d)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.n_bup; q += gridDim.x * blockDim.x)
+        d.bup[q] = __double_as_longlong(d.x[__ldg(d.var_list + q)]) == 0 ? 1 : 0;
+}
+
 // Selective re-evaluation of the binary flips.  k_eval_bin_lazy recomputes the
 // kept score and violation change of the queued positions (all of them when
 // lz_full); k_bin_scan applies tabu and aspiration to the kept values of every
@@ -2397,15 +2636,17 @@ __device__ long long tighten_cutoff(const Dev &d, Ctl *c, long long it)
 
 // End of an iteration (one thread): violation count, x and the reverse
 // direction's tabu stamp after a move, counters, best count, feasibility, the
-// objective cutoff and the run's stop condition.  Returns true when a cutoff
+// objective cutoff and the run's stop condition (q: the moved variable's
+// position).  Returns true when a cutoff
 // solution was recorded (the caller's CTA then copies x to x_best).
-__device__ bool finish_iteration(const Dev &d, Ctl *c, int var, long long delta)
+__device__ bool finish_iteration(const Dev &d, Ctl *c, int var, int q, long long delta)
 {
     long long nv = c->nviol + delta;
     c->nviol = nv;
     const long long it = c->iter;
     if (var >= 0) {
         d.x[var] = c->mv_new;
+        if (q < d.n_bup) d.bup[q] = __double_as_longlong(c->mv_new) == 0 ? 1 : 0;
         const int stamp = (int)(it + 1 + d.tenure);
         if (c->mv_new > c->mv_old) d.tabu_dec[var] = stamp;
         else d.tabu_inc[var] = stamp;
@@ -2508,7 +2749,7 @@ __global__ void __launch_bounds__(kApplyMoveThreads) k_apply_move(Dev d, int gat
                 c->apply_ticket = 0;
             }
         }
-        s_snap = last && finish_iteration(d, c, var, t);
+        s_snap = last && finish_iteration(d, c, var, q, t);
     }
     __syncthreads();
     if (s_snap) snapshot_x(d);
@@ -2542,7 +2783,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bump(Dev d, int gate)
         if (last) {
             __threadfence();
             c->apply_ticket = 0;
-            snap = finish_iteration(d, c, -1, 0);
+            snap = finish_iteration(d, c, -1, -1, 0);
         }
         s_snap = snap;
     }
@@ -2945,6 +3186,7 @@ cudaError_t setup_kernel_attributes(const LaunchPlan &p)
     if (e == cudaSuccess && p.hist_smem > 0) e = raise_smem_limit((const void *)k_eval_hist, 3, p.hist_smem);
     if (e == cudaSuccess && p.n_lgen > 0) e = raise_smem_limit((const void *)k_long_gen, 4, long_gen_smem());
     if (e == cudaSuccess && p.bin_rows) e = raise_smem_limit((const void *)k_eval_bin_rows, 5, kRbSmem);
+    if (e == cudaSuccess && p.bin_blk) e = raise_smem_limit((const void *)k_eval_bin_blk, 7, blk_smem(p.bb.rows));
     return e;
 }
 
@@ -3014,6 +3256,11 @@ cudaError_t launch_eval_gated(const Dev &d, const LaunchPlan &p, const VarOut &o
     } else if (p.n_bin && p.bin_rows) {
         PROF(0, 0);
         if (e == cudaSuccess) e = launch_bin_rows(d, p, o, gate, st);
+        PROF(0, 1);
+    } else if (p.n_bin && p.bin_blk) {
+        PROF(0, 0);
+        k_eval_bin_blk<<<p.bb.n_items, kBlkThreads, blk_smem(p.bb.rows), st>>>(d, p.bb, gate);
+        k_bin_blk_final<<<p.bb.n_fin, kBlkFinThreads, 0, st>>>(d, p.bb, p.bin_cols, o, gate);
         PROF(0, 1);
     } else if (p.n_bin) {
         PROF(0, 0);
@@ -3092,6 +3339,7 @@ cudaError_t launch_set_move(const Dev &d, int var, double nv, cudaStream_t st)
 cudaError_t launch_residuals(const Dev &d, const int *w, cudaStream_t st)
 {
     k_canon_x<<<grid_for(d.n, 256), 256, 0, st>>>(d);
+    if (d.n_bup > 0) k_bup_init<<<grid_for(d.n_bup, 256), 256, 0, st>>>(d);
     const int n_fp = d.m - d.n_res_int;
     const int fp_ctas = (n_fp + 31) / 32;
     const int int_ctas = d.n_res_int > 0 ? std::min((d.n_res_int + kResThreads / 32 - 1) / (kResThreads / 32), 152 * 3) : 0;
